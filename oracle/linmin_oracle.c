@@ -1,0 +1,411 @@
+/*
+ * FP64 CPU oracle for LinMin's per-pixel fully constrained unmixing.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+ * CUDA path is checked against.  Only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product path never calls it
+ * and shares no code, header or table with it.
+ *
+ * What it computes (Schmidt, Legendre & Le Mouelic, "LinMin"):
+ *
+ *   Sec. 2.1, eq. LinearMixing / UnconstrainedProblem: least squares fit of
+ *     one observed spectrum y (L bands) by the library S (P spectra).
+ *   Sec. 2.2, eqs. NonNegativity and SumToOne: abundances x >= 0, sum x = 1
+ *     (FCLS).
+ *   Sec. 2.3, eq. RenormalizedProblem: the criterion is whitened by the noise
+ *     covariance, C^-1 = L L^T, X' = X L, S' = S L.  For a diagonal C with
+ *     per-band standard deviation sigma_l this is W = diag(1/sigma_l).
+ *   Sec. 2.2 (IPLS, primal-dual interior point): the paper cites the solver
+ *     without stating it.  The reading used here is the textbook Mehrotra
+ *     predictor-corrector primal-dual method for the convex QP
+ *
+ *        minimise f(x) = 1/2 |W (y - S^T x)|^2   s.t.  x >= 0,  1^T x = 1
+ *
+ *     i.e. 1/2 x^T G x - c^T x + 1/2 s with G = S W^2 S^T, c = S W^2 y,
+ *     s = y^T W^2 y.  The paper's F has no factor 1/2; the minimiser is the
+ *     same.  Each Newton system is the bordered KKT system
+ *
+ *        [ G + X^-1 Lambda   1 ] [dx ]   [ -r_d - X^-1 r_c ]
+ *        [ 1^T               0 ] [dnu] = [ -r_p            ]
+ *
+ *     with r_d = G x - c - lambda + nu 1, r_p = 1^T x - 1, r_c = x o lambda
+ *     - sigma mu 1, solved as a whole by Gaussian elimination with partial
+ *     pivoting (G alone may be singular: the minimiser is unique when
+ *     rank [S^T; 1^T] = P, Sec. 5, not when G is regular).
+ *   Sec. 2.3, last paragraph: "the error on the mixing coefficient is
+ *     provided by the Hessian".  Reading: the standard deviation of the
+ *     estimator under the Gaussian noise model, i.e. the square root of the
+ *     diagonal of the top-left block of [[G_SS, 1],[1^T, 0]]^-1 on the
+ *     support S of the solution, and 0 off the support.
+ *   RMS (Sec. 3.1, Sec. 4 detection conditions): sqrt(mean_l (y - S^T x)^2),
+ *     unwhitened.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ prep */
+
+/* Whitened Gram matrix G (P x P, row-major) and B = W^2 S (P x L) of the
+ * library S (P x L row-major: row j is spectrum j).  Sec. 2.3. */
+int oracle_prep(int L, int P, const float *S, const float *sigma, double *G,
+                double *B)
+{
+    if (L <= 0 || P <= 0) return 1;
+    for (int l = 0; l < L; l++)
+        if (!(sigma[l] > 0.0f)) return 2;
+    for (int i = 0; i < P; i++) {
+        for (int j = 0; j <= i; j++) {
+            long double acc = 0.0L;
+            for (int l = 0; l < L; l++) {
+                long double w = 1.0L / (long double)sigma[l];
+                acc += ((long double)S[(size_t)i * L + l] * w) *
+                       ((long double)S[(size_t)j * L + l] * w);
+            }
+            G[(size_t)i * P + j] = (double)acc;
+            G[(size_t)j * P + i] = (double)acc;
+        }
+        for (int l = 0; l < L; l++) {
+            long double w = 1.0L / (long double)sigma[l];
+            B[(size_t)i * L + l] = (double)((long double)S[(size_t)i * L + l] * w * w);
+        }
+    }
+    return 0;
+}
+
+/* c = B y (P values) and s = y^T W^2 y for one pixel y. */
+void oracle_project(int L, int P, const double *B, const float *sigma,
+                    const float *y, double *c, double *s)
+{
+    for (int j = 0; j < P; j++) {
+        long double acc = 0.0L;
+        for (int l = 0; l < L; l++) acc += (long double)B[(size_t)j * L + l] * y[l];
+        c[j] = (double)acc;
+    }
+    long double ss = 0.0L;
+    for (int l = 0; l < L; l++) {
+        long double w = (long double)y[l] / (long double)sigma[l];
+        ss += w * w;
+    }
+    *s = (double)ss;
+}
+
+/* ----------------------------------------------------- dense linear algebra */
+
+/* LU with partial pivoting of the n x n row-major matrix M, in place.
+ * Returns 0, or 1 when a pivot is exactly zero. */
+static int lu_factor(int n, double *M, int *piv)
+{
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = fabs(M[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; i++) {
+            double v = fabs(M[(size_t)i * n + k]);
+            if (v > best) { best = v; p = i; }
+        }
+        piv[k] = p;
+        if (best == 0.0) return 1;
+        if (p != k)
+            for (int j = 0; j < n; j++) {
+                double t = M[(size_t)k * n + j];
+                M[(size_t)k * n + j] = M[(size_t)p * n + j];
+                M[(size_t)p * n + j] = t;
+            }
+        for (int i = k + 1; i < n; i++) {
+            double m = M[(size_t)i * n + k] / M[(size_t)k * n + k];
+            M[(size_t)i * n + k] = m;
+            for (int j = k + 1; j < n; j++) M[(size_t)i * n + j] -= m * M[(size_t)k * n + j];
+        }
+    }
+    return 0;
+}
+
+static void lu_solve(int n, const double *M, const int *piv, double *b)
+{
+    for (int k = 0; k < n; k++) {
+        int p = piv[k];
+        if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < i; j++) b[i] -= M[(size_t)i * n + j] * b[j];
+    for (int i = n - 1; i >= 0; i--) {
+        for (int j = i + 1; j < n; j++) b[i] -= M[(size_t)i * n + j] * b[j];
+        b[i] /= M[(size_t)i * n + i];
+    }
+}
+
+/* ------------------------------------------------------------- IPLS (FP64) */
+
+/* Largest step in (0, 1] keeping v + a dv >= 0 (fraction-to-boundary). */
+static double max_step(int P, const double *v, const double *dv)
+{
+    double a = 1.0;
+    for (int i = 0; i < P; i++)
+        if (dv[i] < 0.0) {
+            double t = -v[i] / dv[i];
+            if (t < a) a = t;
+        }
+    return a;
+}
+
+/* Status codes of oracle_fcls. */
+#define OR_OK 0
+#define OR_MAXITER 1
+#define OR_SINGULAR 2
+
+/*
+ * Mehrotra predictor-corrector IPM for min 1/2 x'Gx - c'x + s/2,
+ * x >= 0, 1'x = 1.  G is P x P row-major.  Writes x, lambda, nu, the
+ * iteration count and the final mu = x'lambda/P.  Returns a status code.
+ *
+ * Start: x = 1/P, lambda = max(|c|_inf / P, 1e-3) 1, nu = 0.
+ * Stop:  |r_d|_inf <= 1e-12 (1 + |c|_inf), |r_p| <= 1e-14,
+ *        mu <= 1e-13 (1 + |f|), or max_iter iterations.
+ * Step:  alpha_p, alpha_d = min(1, 0.995 * max feasible), primal and dual
+ *        separately.
+ */
+int oracle_fcls(int P, const double *G, const double *c, double s, int max_iter,
+                double *x, double *lam, double *nu_out, int *iters_out,
+                double *mu_out)
+{
+    const int n = P + 1;
+    double *K = malloc(sizeof(double) * n * n);
+    int *piv = malloc(sizeof(int) * n);
+    double *rd = malloc(sizeof(double) * P), *gx = malloc(sizeof(double) * P);
+    double *rhs = malloc(sizeof(double) * n), *dxa = malloc(sizeof(double) * P);
+    double *dla = malloc(sizeof(double) * P), *dx = malloc(sizeof(double) * P);
+    double *dl = malloc(sizeof(double) * P), *rc = malloc(sizeof(double) * P);
+    double *tmp = malloc(sizeof(double) * P);
+    int status = OR_MAXITER, it = 0;
+
+    double cinf = 0.0;
+    for (int i = 0; i < P; i++) cinf = fmax(cinf, fabs(c[i]));
+    double lam0 = fmax(cinf / P, 1e-3);
+    double nu = 0.0;
+    for (int i = 0; i < P; i++) { x[i] = 1.0 / P; lam[i] = lam0; }
+    double mu = 0.0;
+
+    for (it = 0; it <= max_iter; it++) {
+        /* residuals */
+        double rp = -1.0, rdinf = 0.0, xgx = 0.0, cx = 0.0;
+        mu = 0.0;
+        for (int i = 0; i < P; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < P; j++) acc += G[(size_t)i * P + j] * x[j];
+            gx[i] = acc;
+            rd[i] = acc - c[i] - lam[i] + nu;
+            rdinf = fmax(rdinf, fabs(rd[i]));
+            rp += x[i];
+            mu += x[i] * lam[i];
+            xgx += x[i] * acc;
+            cx += c[i] * x[i];
+        }
+        mu /= P;
+        double f = 0.5 * xgx - cx + 0.5 * s;
+        if (rdinf <= 1e-12 * (1.0 + cinf) && fabs(rp) <= 1e-14 &&
+            mu <= 1e-13 * (1.0 + fabs(f))) {
+            status = OR_OK;
+            break;
+        }
+        if (it == max_iter) break;
+
+        /* bordered KKT matrix, factored once for both solves */
+        for (int i = 0; i < P; i++) {
+            for (int j = 0; j < P; j++) K[(size_t)i * n + j] = G[(size_t)i * P + j];
+            K[(size_t)i * n + i] += lam[i] / x[i];
+            K[(size_t)i * n + P] = 1.0;
+            K[(size_t)P * n + i] = 1.0;
+        }
+        K[(size_t)P * n + P] = 0.0;
+        if (lu_factor(n, K, piv)) { status = OR_SINGULAR; break; }
+
+        /* predictor (affine scaling): r_c = x o lambda */
+        for (int i = 0; i < P; i++) rhs[i] = -rd[i] - lam[i];
+        rhs[P] = -rp;
+        lu_solve(n, K, piv, rhs);
+        for (int i = 0; i < P; i++) {
+            dxa[i] = rhs[i];
+            dla[i] = -lam[i] - lam[i] / x[i] * dxa[i];
+        }
+        double ap = max_step(P, x, dxa), ad = max_step(P, lam, dla);
+        double mua = 0.0;
+        for (int i = 0; i < P; i++) mua += (x[i] + ap * dxa[i]) * (lam[i] + ad * dla[i]);
+        mua /= P;
+        double sig = pow(mua / mu, 3.0);
+
+        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu */
+        for (int i = 0; i < P; i++) {
+            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
+            rhs[i] = -rd[i] - rc[i] / x[i];
+        }
+        rhs[P] = -rp;
+        lu_solve(n, K, piv, rhs);
+        double dnu = rhs[P];
+        for (int i = 0; i < P; i++) {
+            dx[i] = rhs[i];
+            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+        }
+        ap = fmin(1.0, 0.995 * max_step(P, x, dx));
+        ad = fmin(1.0, 0.995 * max_step(P, lam, dl));
+        for (int i = 0; i < P; i++) {
+            x[i] += ap * dx[i];
+            lam[i] += ad * dl[i];
+        }
+        nu += ad * dnu;
+        (void)tmp;
+    }
+    /* x <- max(x, 0) / sum */
+    double sum = 0.0;
+    for (int i = 0; i < P; i++) { if (x[i] < 0.0) x[i] = 0.0; sum += x[i]; }
+    for (int i = 0; i < P; i++) x[i] /= sum;
+
+    *nu_out = nu;
+    *iters_out = it;
+    *mu_out = mu;
+    free(K); free(piv); free(rd); free(gx); free(rhs); free(dxa);
+    free(dla); free(dx); free(dl); free(rc); free(tmp);
+    return status;
+}
+
+/* --------------------------------------------------------- uncertainty */
+
+/* Support of the final iterate: i is active when its barrier term
+ * lambda_i / x_i is below its curvature G_ii. */
+int oracle_support(int P, const double *G, const double *x, const double *lam,
+                   int *in_S)
+{
+    int k = 0;
+    for (int i = 0; i < P; i++) {
+        in_S[i] = lam[i] < x[i] * G[(size_t)i * P + i];
+        k += in_S[i];
+    }
+    return k;
+}
+
+/* sigma_x: sqrt of the diagonal of the top-left block of
+ * [[G_SS, 1],[1^T, 0]]^-1 on the support S, 0 elsewhere.  Returns 0, or 1
+ * when the bordered system on S is singular (sx is then set to NaN on S). */
+int oracle_sigma_x(int P, const double *G, const int *in_S, double *sx)
+{
+    int k = 0;
+    int *idx = malloc(sizeof(int) * P);
+    for (int i = 0; i < P; i++) if (in_S[i]) idx[k++] = i;
+    for (int i = 0; i < P; i++) sx[i] = 0.0;
+    int n = k + 1, bad = 0;
+    double *K = malloc(sizeof(double) * n * n);
+    int *piv = malloc(sizeof(int) * n);
+    double *e = malloc(sizeof(double) * n);
+    for (int a = 0; a < k; a++) {
+        for (int b = 0; b < k; b++) K[(size_t)a * n + b] = G[(size_t)idx[a] * P + idx[b]];
+        K[(size_t)a * n + k] = 1.0;
+        K[(size_t)k * n + a] = 1.0;
+    }
+    K[(size_t)k * n + k] = 0.0;
+    if (k == 0 || lu_factor(n, K, piv)) {
+        bad = 1;
+        for (int a = 0; a < k; a++) sx[idx[a]] = NAN;
+    } else {
+        for (int a = 0; a < k; a++) {
+            for (int b = 0; b < n; b++) e[b] = (a == b) ? 1.0 : 0.0;
+            lu_solve(n, K, piv, e);
+            /* e[a] = [K^-1]_aa; it is >= 0 up to rounding */
+            sx[idx[a]] = sqrt(fmax(e[a], 0.0));
+        }
+    }
+    free(idx); free(K); free(piv); free(e);
+    return bad;
+}
+
+/* Unwhitened RMS of the fit: sqrt(mean_l (y_l - sum_j x_j S_jl)^2). */
+double oracle_rms(int L, int P, const float *S, const double *x, const float *y)
+{
+    long double acc = 0.0L;
+    for (int l = 0; l < L; l++) {
+        long double m = 0.0L;
+        for (int j = 0; j < P; j++) m += (long double)x[j] * S[(size_t)j * L + l];
+        long double r = (long double)y[l] - m;
+        acc += r * r;
+    }
+    return (double)sqrtl(acc / L);
+}
+
+/* ------------------------------------------------------------ whole cube */
+
+typedef struct {
+    int L, P, max_iter;
+    const float *S, *sigma, *X;
+    const double *G, *B;
+    long long lo, hi;
+    double *x, *sx, *rms, *lam, *nu, *mu;
+    int *iters, *status, *ksup;
+} job_t;
+
+static void *unmix_range(void *arg)
+{
+    job_t *j = (job_t *)arg;
+    int P = j->P, L = j->L;
+    double *c = malloc(sizeof(double) * P);
+    double *lam = malloc(sizeof(double) * P);
+    int *in_S = malloc(sizeof(int) * P);
+    for (long long n = j->lo; n < j->hi; n++) {
+        const float *y = j->X + (size_t)n * L;
+        double s, nu, mu;
+        int it;
+        double *x = j->x + (size_t)n * P;
+        oracle_project(L, P, j->B, j->sigma, y, c, &s);
+        int st = oracle_fcls(P, j->G, c, s, j->max_iter, x, lam, &nu, &it, &mu);
+        int k = oracle_support(P, j->G, x, lam, in_S);
+        if (oracle_sigma_x(P, j->G, in_S, j->sx + (size_t)n * P)) st |= 4;
+        j->rms[n] = oracle_rms(L, P, j->S, x, y);
+        j->iters[n] = (st & 3) == OR_OK ? it : -it - 1;
+        if (j->status) j->status[n] = st;
+        if (j->ksup) j->ksup[n] = k;
+        if (j->lam) memcpy(j->lam + (size_t)n * P, lam, sizeof(double) * P);
+        if (j->nu) j->nu[n] = nu;
+        if (j->mu) j->mu[n] = mu;
+    }
+    free(c); free(lam); free(in_S);
+    return NULL;
+}
+
+int oracle_nproc(void)
+{
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int)n : 1;
+}
+
+/*
+ * Unmix N pixels of the pixel-major cube X (N x L) against the library S
+ * (P x L).  Outputs (caller-allocated): x and sx (N x P), rms (N), iters (N,
+ * negative = did not converge); optional (may be NULL): lam (N x P), nu, mu,
+ * status, ksup (N).  nthreads <= 0 uses every online core.  Returns 0, or a
+ * non-zero code for invalid arguments.
+ */
+int oracle_unmix(int L, int P, const float *S, const float *sigma, long long N,
+                 const float *X, int max_iter, int nthreads, double *x,
+                 double *sx, double *rms, int *iters, double *lam, double *nu,
+                 double *mu, int *status, int *ksup)
+{
+    if (N < 0 || L <= 0 || P <= 0) return 1;
+    if (N == 0) return 0;
+    double *G = malloc(sizeof(double) * P * P);
+    double *B = malloc(sizeof(double) * (size_t)P * L);
+    int rc = oracle_prep(L, P, S, sigma, G, B);
+    if (rc) { free(G); free(B); return rc; }
+    if (nthreads <= 0) nthreads = oracle_nproc();
+    if ((long long)nthreads > N) nthreads = (int)N;
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    job_t *jobs = malloc(sizeof(job_t) * nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        job_t j = {L, P, max_iter, S, sigma, X, G, B,
+                   N * t / nthreads, N * (t + 1) / nthreads,
+                   x, sx, rms, lam, nu, mu, iters, status, ksup};
+        jobs[t] = j;
+        pthread_create(&th[t], NULL, unmix_range, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    free(th); free(jobs); free(G); free(B);
+    return 0;
+}

@@ -1,0 +1,238 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle (``oracle/``) against something other than
+itself: exhaustive support enumeration (the combination search of Sec. 2.1
+reused as a check), the Frank-Wolfe/KKT optimality certificates of the
+convex problem of Sec. 2.2, closed forms (P = 1, P = 2, interior SCLS),
+exact noise-free mixtures, invariances of the whitened problem of Sec. 2.3,
+a Monte-Carlo check of the "error provided by the Hessian" (Sec. 2.3), the
+RMS of the fit, and an independent NNLS-based FCLS (scipy).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import _pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _tiny_library(rng, P, L, with_extras):
+    if with_extras and P >= 6:
+        S = synth.library(rng, L, P - 4, 4)
+    else:
+        S = synth.library(rng, L, P, 0)
+    return S.astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_brute_force_small_P(seed):
+    """x equals the exhaustive-support minimiser; sigma_x equals the bordered
+    inverse on that support."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    P = int(rng.integers(2, 11))
+    L = int(rng.integers(P + 2, 4 * P + 8))
+    S = _tiny_library(rng, P, L, with_extras=seed % 2 == 0)
+    if not synth.check_unique(S):
+        pytest.skip("drawn library not unique")
+    sigma = rng.uniform(0.002, 0.02, size=L).astype(np.float32)
+    N = 4
+    xt = synth.abundances(rng, N, P, P, min(3, P))
+    X = (xt @ S.astype(np.float64) + rng.standard_normal((N, L)) * sigma).astype(np.float32)
+    r = oracle.unmix(S, sigma, X, nthreads=1)
+    assert np.all(r["iters"] >= 0)
+    for n in range(N):
+        G, c, s = _pins.qp_terms(S, sigma, X[n])
+        xb = _pins.brute_force(G, c, s)
+        np.testing.assert_allclose(r["x"][n], xb, atol=2e-8, rtol=0)
+        f_or = _pins.objective(G, c, s, r["x"][n])
+        f_bf = _pins.objective(G, c, s, xb)
+        assert f_or - f_bf <= 1e-9 * max(1.0, abs(f_bf))
+        idx = np.flatnonzero(xb > 1e-9)
+        lam = r["lam"][n]
+        # strictly complementary pixels only: the support is then unambiguous
+        ratio = lam / np.maximum(r["x"][n], 1e-300) / np.diag(G)
+        if np.all((ratio < 1e-4) | (ratio > 1e4)):
+            np.testing.assert_allclose(r["sx"][n], _pins.support_sigma(G, idx),
+                                       rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("spec", synth.WORKLOADS, ids=lambda s: s.name)
+def test_kkt_certificate_on_workloads(spec):
+    """Feasible, Frank-Wolfe gap ~ 0 and KKT conditions on sampled pixels."""
+    cube = synth.make_cube(spec, n_pix=400)
+    r = oracle.unmix(cube.S, cube.sigma, cube.X)
+    assert np.all(r["iters"] >= 0), "oracle hit its iteration cap"
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    scale = np.max(np.diag(G))
+    for n in range(cube.N):
+        x = r["x"][n]
+        c = B @ cube.X[n].astype(np.float64)
+        assert abs(x.sum() - 1.0) <= 1e-12
+        assert x.min() >= 0.0
+        gap = _pins.fw_gap(G, c, x)
+        assert gap <= 1e-9 * scale, gap
+        stat, dual = _pins.kkt_violation(G, c, x, support_tol=1e-9)
+        assert stat <= 1e-6 * scale and dual <= 1e-6 * scale
+
+
+def test_golden_exact_mixtures():
+    """Noise-free dyadic mixtures (exact in fp32) are recovered to 1e-10.
+
+    Where x has zeros the problem is degenerate (zero residual makes the
+    multiplier of every inactive coordinate zero as well): an interior-point
+    iterate then approaches x_i = lambda_i = 0 at the rate sqrt(mu), and the
+    stopping rule mu <= 1e-13 (1 + |f|) bounds the error by ~3e-7; 1e-8 is
+    asserted there."""
+    with open(os.path.join(GOLDEN, "dyadic_mixtures.json")) as f:
+        gold = json.load(f)
+    for case in gold["cases"]:
+        S = (np.array(case["S_num"], dtype=np.float64) / case["S_den"]).astype(np.float32)
+        x = np.array(case["x"])
+        y64 = x @ S.astype(np.float64)
+        y = y64.astype(np.float32)
+        assert np.array_equal(y.astype(np.float64), y64), "fixture not exact in fp32"
+        sigma = np.full(case["L"], case["sigma"], dtype=np.float32)
+        r = oracle.unmix(S, sigma, y[None, :])
+        tol = 1e-10 if np.all(x > 0) else 1e-8
+        np.testing.assert_allclose(r["x"][0], x, atol=tol, rtol=0)
+        assert r["rms"][0] <= 1e-8
+
+
+def test_closed_form_P1():
+    rng = np.random.Generator(np.random.PCG64(5))
+    S = rng.uniform(0.2, 0.6, size=(1, 30)).astype(np.float32)
+    sigma = np.full(30, 0.01, dtype=np.float32)
+    X = rng.uniform(0.0, 1.0, size=(3, 30)).astype(np.float32)
+    r = oracle.unmix(S, sigma, X)
+    np.testing.assert_array_equal(r["x"], np.ones((3, 1)))
+    # one active coordinate: K = [[g, 1],[1, 0]] has K^-1_00 = 0
+    np.testing.assert_allclose(r["sx"], 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_closed_form_P2(seed):
+    """x_1 = clamp((c1 - c2 - G12 + G22) / (G11 - 2 G12 + G22), 0, 1)."""
+    rng = np.random.Generator(np.random.PCG64(50 + seed))
+    L = 40
+    S = rng.uniform(0.2, 0.6, size=(2, L)).astype(np.float32)
+    sigma = rng.uniform(0.002, 0.02, size=L).astype(np.float32)
+    # abundances across [-0.3, 1.3]: both clamped and interior cases
+    a = np.linspace(-0.3, 1.3, 9)
+    xt = np.stack([a, 1 - a], 1)
+    X = (xt @ S.astype(np.float64)).astype(np.float32)
+    r = oracle.unmix(S, sigma, X)
+    for n in range(len(a)):
+        G, c, _ = _pins.qp_terms(S, sigma, X[n])
+        x1 = (c[0] - c[1] - G[0, 1] + G[1, 1]) / (G[0, 0] - 2 * G[0, 1] + G[1, 1])
+        x1 = min(max(x1, 0.0), 1.0)
+        np.testing.assert_allclose(r["x"][n], [x1, 1 - x1], atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_closed_form_interior_scls(seed):
+    """All-positive solution: x = G^-1 (c - nu 1), nu = (1'G^-1 c - 1)/(1'G^-1 1)
+    (the sum-to-one constrained LS of Sec. 2.2)."""
+    rng = np.random.Generator(np.random.PCG64(70 + seed))
+    P, L = 5, 60
+    S = synth.library(rng, L, P, 0).astype(np.float32)
+    sigma = np.full(L, 0.001, dtype=np.float32)
+    xt = np.array([0.3, 0.25, 0.2, 0.15, 0.1])
+    X = (xt @ S.astype(np.float64) + rng.standard_normal(L) * 0.001).astype(np.float32)[None]
+    r = oracle.unmix(S, sigma, X)
+    G, c, _ = _pins.qp_terms(S, sigma, X[0])
+    Gi_c = np.linalg.solve(G, c)
+    Gi_1 = np.linalg.solve(G, np.ones(P))
+    nu = (Gi_c.sum() - 1.0) / Gi_1.sum()
+    x = Gi_c - nu * Gi_1
+    assert np.all(x > 0)
+    np.testing.assert_allclose(r["x"][0], x, atol=1e-9)
+    np.testing.assert_allclose(r["sx"][0], _pins.support_sigma(G, np.arange(P)), rtol=1e-7)
+
+
+def test_sigma_scaling_invariance():
+    """C -> k^2 C leaves x and the RMS unchanged and scales sigma_x by k."""
+    cube = synth.make_cube(synth.OMEGA_262K, n_pix=64)
+    base = oracle.unmix(cube.S, cube.sigma, cube.X)
+    for k in (0.125, 8.0):
+        r = oracle.unmix(cube.S, (cube.sigma * k).astype(np.float32), cube.X)
+        np.testing.assert_allclose(r["x"], base["x"], atol=1e-8)
+        np.testing.assert_allclose(r["rms"], base["rms"], rtol=1e-7)
+        ok = (r["ksup"] == base["ksup"])
+        np.testing.assert_allclose(r["sx"][ok], k * base["sx"][ok], rtol=1e-6, atol=1e-12)
+
+
+def test_permutation_equivariance():
+    cube = synth.make_cube(synth.FCLS_1K, n_pix=32)
+    perm = np.random.Generator(np.random.PCG64(3)).permutation(cube.P)
+    base = oracle.unmix(cube.S, cube.sigma, cube.X)
+    r = oracle.unmix(cube.S[perm], cube.sigma, cube.X)
+    np.testing.assert_allclose(r["x"], base["x"][:, perm], atol=1e-9)
+    np.testing.assert_allclose(r["sx"], base["sx"][:, perm], rtol=1e-6, atol=1e-12)
+
+
+def test_monte_carlo_uncertainty():
+    """Empirical std of x over noise redraws matches sigma_x within 5 %
+    (Sec. 2.3: error from the Hessian, read as the estimator's std; the
+    paper's F without 1/2 would make it sqrt(2) too small)."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    P, L = 4, 80
+    S = synth.library(rng, L, P, 0).astype(np.float32)
+    sigma = rng.uniform(0.002, 0.004, size=L).astype(np.float32)
+    xt = np.array([0.35, 0.3, 0.2, 0.15])
+    R = 2000
+    X = (xt @ S.astype(np.float64) + rng.standard_normal((R, L)) * sigma).astype(np.float32)
+    r = oracle.unmix(S, sigma, X)
+    assert np.all(r["ksup"] == P), "support not stable: choose a smaller noise"
+    emp = r["x"].std(axis=0, ddof=1)
+    pred = r["sx"].mean(axis=0)
+    np.testing.assert_allclose(emp, pred, rtol=0.05)
+    assert np.all(np.abs(r["x"].mean(axis=0) - xt) < 4 * pred / np.sqrt(R) + 1e-12)
+
+
+def test_rms_definition_and_noise_level():
+    """RMS = |y - S^T x| / sqrt(L) (unwhitened) and ~ the noise level on
+    exact-model data (Sec. 3.1: RMS compatible with the noise)."""
+    cube = synth.make_cube(synth.FCLS_1K, n_pix=300)
+    r = oracle.unmix(cube.S, cube.sigma, cube.X)
+    fit = r["x"] @ cube.S.astype(np.float64)
+    ref = np.sqrt(np.mean((cube.X.astype(np.float64) - fit) ** 2, axis=1))
+    np.testing.assert_allclose(r["rms"], ref, rtol=1e-10)
+    noise = float(np.sqrt(np.mean(cube.sigma.astype(np.float64) ** 2)))
+    assert abs(r["rms"].mean() / noise - 1.0) < 0.05
+
+
+def test_against_augmented_nnls():
+    """FCLS as NNLS with a heavily weighted sum-to-one row (Heinz-Chang);
+    its error is O(1/delta^2), independent of the interior-point code."""
+    nnls = pytest.importorskip("scipy.optimize").nnls
+    cube = synth.make_cube(synth.OMEGA_262K, n_pix=40)
+    r = oracle.unmix(cube.S, cube.sigma, cube.X)
+    S = cube.S.astype(np.float64)
+    w = 1.0 / cube.sigma.astype(np.float64)
+    Aw = (S * w).T
+    delta = 1e4 * np.sqrt(np.max(np.sum(Aw * Aw, axis=0)))
+    Aaug = np.vstack([Aw, delta * np.ones((1, cube.P))])
+    for n in range(cube.N):
+        yaug = np.concatenate([cube.X[n].astype(np.float64) * w, [delta]])
+        xn, _ = nnls(Aaug, yaug, maxiter=50 * cube.P)
+        np.testing.assert_allclose(r["x"][n], xn, atol=2e-6)
+
+
+def test_non_unique_library_detected():
+    """The paper's +-cos/+-sin extras (Appendix, ids 37-44) sum to zero in
+    pairs; two such pairs give a null direction d of S^T with 1^T d = 0, so
+    rank [S^T; 1^T] < P and the minimiser is not unique.  One pair alone
+    (1^T d = 2) or the four level/slope extras keep it unique."""
+    L = 64
+    lam = synth.wavelengths(L)
+    u = (lam - lam[0]) / (lam[-1] - lam[0])
+    c, s = np.cos(np.pi * u / 2), np.sin(np.pi * u / 2)
+    base = [np.ones(L), 0.3 + 0.1 * u]
+    assert not synth.check_unique(np.stack(base + [c, -c, s, -s]))
+    assert synth.check_unique(np.stack(base + [c, -c]))
+    assert synth.check_unique(synth.extra_spectra(L))
