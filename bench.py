@@ -1,0 +1,298 @@
+"""Benchmark: pixels/s of fully constrained IPLS unmixing on the OMEGA-shaped
+synthetic cube (262,144 pixels, L = 184 bands, P = 36 spectra: 32 minerals
++ 4 level/slope spectra, per-band sigma in [0.002, 0.02]).
+
+One step = one linmin_unmix call over the whole cube (library preparation,
+double-float projection, interior-point solve in two residual phases,
+fp64 support refinement with uncertainties, RMS), inputs resident in HBM.
+The cube (193 MB) is larger than L2 (129 MB), so no flush between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank unmixes its own cube (weak scaling, no collective
+on the data path); the timing is the max over ranks.  ``--impl reference``
+times the FP64 CPU oracle on a bounded pixel sample of the same cube.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+SPEC = synth.OMEGA_262K
+METRIC = "pixels/s IPLS unmix at <=1e-4 abs err vs FP64 oracle; served p50/p99 latency"
+FP32_LANES_PER_SM = 128
+KERNELS_PER_STEP = 8   # prep x3, projection, IPM x2, refinement, rms
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(cube, target_s: float):
+    """The FP64 oracle, as it stands, on a bounded prefix of the same cube,
+    on every host core."""
+    import oracle
+    n0 = min(cube.N, 1024)
+    t = time.perf_counter()
+    oracle.unmix(cube.S, cube.sigma, cube.X[:n0], extras=False)
+    rate = n0 / max(time.perf_counter() - t, 1e-6)
+    n = int(min(cube.N, max(n0, rate * target_s)))
+    t = time.perf_counter()
+    oracle.unmix(cube.S, cube.sigma, cube.X[:n], extras=False)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "pixels/s", "cores": oracle.nproc(), "kind": "oracle",
+            "sample": f"first {n} of {cube.N} pixels of {SPEC.name}, {dt:.1f} s"}
+
+
+def run_reference(args, cube):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    n = int(min(cube.N, 4096))
+    for _ in range(args.warmup):
+        oracle.unmix(cube.S, cube.sigma, cube.X[:256], extras=False)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.unmix(cube.S, cube.sigma, cube.X[:n], extras=False)
+        times.append(time.perf_counter() - t)
+    tot = sum(times)
+    value = n * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pixels/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": SPEC.name, "pixels": SPEC.n_pix, "L": SPEC.L,
+                       "P": SPEC.P, "step_sample_pixels": n},
+            "cpu_baseline": {"value": value, "unit": "pixels/s", "cores": oracle.nproc(),
+                             "kind": "oracle",
+                             "sample": f"first {n} of {cube.N} pixels per step"},
+            "e2e": {"value": value, "unit": "pixels/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    cube = synth.make_cube(SPEC)
+    if args.impl == "reference":
+        run_reference(args, cube)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1402_2518_gb300 as pkg
+    pkg.load()
+    stream = torch.cuda.Stream(device=dev)
+    um = pkg.Unmixer(torch.from_numpy(cube.S).to(dev), stream=stream, profile=True)
+    X = torch.from_numpy(cube.X).to(dev)
+    sig = torch.from_numpy(cube.sigma).to(dev)
+    N, P, L = cube.N, cube.P, cube.L
+    x = torch.empty((N, P), device=dev)
+    sx = torch.empty((N, P), device=dev)
+    rms = torch.empty((N,), device=dev)
+    it = torch.empty((N,), dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        pkg.linmin_unmix(um.h, X, N, sig, x, sx, rms, it)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    st, nbad = um.wait()
+    if st not in (0,):
+        raise RuntimeError(f"unmix status {st}: {pkg.linmin_last_error(um.h)}")
+
+    phase_tot = {k: 0.0 for k in pkg.linmin.PHASES}
+    flops_ipm = 0.0
+    iters = it.to(torch.float64).abs()
+    flop_per_iter = P ** 3 / 3.0 + 6.0 * P * P
+    flops_ipm = float(iters.sum().item()) * flop_per_iter
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+            pt = um.phase_times()          # events on the library's stream
+            for k, v in pt.items():
+                phase_tot[k] += v
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    st, nbad = um.wait()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    Xh = torch.from_numpy(cube.X).pin_memory()
+    sgh = torch.from_numpy(cube.sigma).pin_memory()
+    xh = torch.empty((N, P)).pin_memory(); sxh = torch.empty((N, P)).pin_memory()
+    rh = torch.empty((N,)).pin_memory(); ih = torch.empty((N,), dtype=torch.int32).pin_memory()
+    h_host = pkg.linmin_create(cube.S, L, P)
+
+    def step_host():
+        pkg.linmin_unmix(h_host, Xh.numpy(), N, sgh.numpy(), xh.numpy(), sxh.numpy(),
+                         rh.numpy(), ih.numpy())
+
+    step_host()
+    e2e_steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    pkg.linmin_destroy(h_host)
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        dist.barrier() if ws > 1 else None
+        return
+
+    value = N * ws / (ms / 1e3)
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    nsm = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = nsm * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12   # TFLOP/s
+    ipm_ms = (phase_tot["ipm_f32"] + phase_tot["ipm_df"]) / args.steps
+    achieved = flops_ipm / (ipm_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    cpu = None if args.no_cpu_baseline else cpu_baseline(cube, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (double-float residual/projection, fp64 refinement)",
+        "data": "synthetic",
+        "config": {"workload": SPEC.name, "pixels": N, "L": L, "P": P,
+                   "library": "32 minerals + 4 level/slope spectra",
+                   "l2": "inputs larger than L2 (cube 193 MB), no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"kernel": "ipm (float32 + double-float residual phases)",
+                     "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                     "flops_per_iter": flop_per_iter,
+                     "mean_iters": float(iters.mean().item())},
+        "phase_ms": {k: v / args.steps for k, v in phase_tot.items()},
+        "not_converged": nbad,
+        "e2e": {"value": N * ws / e2e_s, "unit": "pixels/s",
+                "h2d_bytes_per_step": N * L * 4 + L * 4,
+                "d2h_bytes_per_step": N * (2 * P + 2) * 4},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    um.close()
+
+
+if __name__ == "__main__":
+    main()

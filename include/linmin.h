@@ -1,0 +1,175 @@
+/*
+ * linmin.h — C ABI of the GB300 (sm_103a) LinMin unmixing library.
+ *
+ * LinMin (Schmidt, Legendre & Le Mouelic, "Minerals detection for
+ * hyperspectral images using adapted linear unmixing: LinMin") fits every
+ * observed spectrum y (L bands) of a cube by a non-negative, sum-to-one
+ * combination x (P abundances) of a shared reference library:
+ *
+ *   Sec. 2.1, eq. LinearMixing:        X = A.S + E, E Gaussian;
+ *   Sec. 2.1, eq. UnconstrainedProblem: least squares criterion;
+ *   Sec. 2.2, eqs. NonNegativity, SumToOne: x >= 0, sum_j x_j = 1 (FCLS);
+ *   Sec. 2.3, eq. RenormalizedProblem: the criterion is whitened by the
+ *     noise covariance; here the covariance is diagonal, given as per-band
+ *     standard deviations sigma_l, i.e. W = diag(1 / sigma_l);
+ *   Sec. 2.2: the problem is solved per pixel by a primal-dual interior
+ *     point least-squares method (IPLS);
+ *   Sec. 2.3 (last paragraph): the uncertainty of each abundance comes from
+ *     the Hessian of the criterion.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Library: float32, P spectra of L bands, spectrum j contiguous
+ *   (library[j * L + l]); this is the paper's S (P x N_lambda, row-major),
+ *   i.e. an L x P column-major matrix.
+ * - Cube: float32, N pixels of L bands, pixel-major (BIP):
+ *   cube[n * L + l]; the paper's X (M x N_lambda).
+ * - sigma: float32, L per-band noise standard deviations, each finite > 0.
+ * - Outputs (caller-allocated, float32 unless stated):
+ *     abundances    N x P, pixel-major, x >= 0 and sum_j x_j = 1;
+ *     uncertainties N x P, the standard deviation of each abundance under
+ *                   the Gaussian noise model: the square root of the
+ *                   diagonal of the top-left block of
+ *                   [[G_SS, 1],[1^T, 0]]^-1 on the support S of the
+ *                   solution, 0 off the support, with G = S W^2 S^T
+ *                   (Hessian of 1/2 |W(y - S^T x)|^2; the paper's
+ *                   criterion has no 1/2, its Hessian is 2G);
+ *     residual_rms  N, sqrt(mean_l (y_l - sum_j x_j S_jl)^2), unwhitened;
+ *     iterations    int32 N, interior-point iterations used; negative when
+ *                   the pixel did not reach the stopping test within
+ *                   max_iter (its last iterate is returned).
+ *   Any output pointer may be NULL; that output is then not written.
+ * - Pointers may be host or device memory (detected per call).  With device
+ *   pointers the call is stream-ordered on the handle's stream and does not
+ *   synchronise; with any host pointer it copies through device buffers and
+ *   synchronises before returning.
+ * - The handle owns all device scratch; it is not thread-safe: use one
+ *   handle per host thread / stream.  Calls on one handle are serialised by
+ *   its stream.
+ * - Errors: every entry point returns a linmin_status; linmin_last_error()
+ *   gives a one-line message for the last failing call on that handle.
+ *   Invalid arguments are detected on the host before any work is queued.
+ */
+#ifndef LINMIN_H
+#define LINMIN_H
+
+#if defined(__GNUC__)
+#define LINMIN_API __attribute__((visibility("default")))
+#else
+#define LINMIN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct linmin_ctx *linmin_handle;
+
+typedef enum {
+    LINMIN_OK = 0,
+    LINMIN_ERR_INVALID = 1,        /* bad size, NULL input, sigma <= 0 / NaN */
+    LINMIN_ERR_OOM = 2,            /* device allocation failed */
+    LINMIN_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    LINMIN_ERR_RANK = 4,           /* rank [S^T; 1^T] < P: minimiser not unique */
+    LINMIN_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    LINMIN_ERR_NOT_CONVERGED = 6,  /* some pixels hit max_iter; see iterations < 0 */
+    LINMIN_ERR_UNSUPPORTED = 7     /* P or L outside the built kernel range */
+} linmin_status;
+
+/* Projection precision (c = S W^2 y).  LINMIN_PROJ_DF accumulates the
+ * products in double-float (two float32 words), which the fully constrained
+ * solve needs to reach 1e-4 on ill-conditioned libraries. */
+enum { LINMIN_PROJ_DF = 0 };
+
+/* Constraint set.  LINMIN_STO: x >= 0 and sum x = 1 (Sec. 2.2, FCLS). */
+enum { LINMIN_STO = 0 };
+
+#define LINMIN_MAX_P 48
+#define LINMIN_MAX_L 4096
+
+typedef struct {
+    int precision;        /* LINMIN_PROJ_DF */
+    int constraint;       /* LINMIN_STO */
+    int max_iter;         /* interior-point iteration cap per pixel (default 100) */
+    float tol;            /* complementarity tolerance: each coordinate ends with
+                             min(x_i, lambda_i / s) <= tol, s = trace(G)/P
+                             (default 1e-9) */
+    float refine_mu;      /* switch to the double-float KKT residual once
+                             mu / s <= refine_mu (default 1e-9) */
+    void *cuda_stream;    /* cudaStream_t the handle runs on; NULL = default */
+    int profile;          /* non-zero: record CUDA events around each phase of
+                             linmin_unmix (see linmin_phase_times); default 0 */
+} linmin_options;
+
+/* Phases of linmin_unmix timed when linmin_options.profile is set. */
+enum {
+    LINMIN_PHASE_PREP = 0,      /* whitening, fp64 Gram, splits (3 kernels) */
+    LINMIN_PHASE_PROJECT = 1,   /* double-float projection c = S W^2 y */
+    LINMIN_PHASE_IPM_F32 = 2,   /* interior point, float32 residual */
+    LINMIN_PHASE_IPM_DF = 3,    /* interior point, double-float residual */
+    LINMIN_PHASE_REFINE = 4,    /* fp64 support solve + uncertainties */
+    LINMIN_PHASE_RMS = 5,       /* residual RMS */
+    LINMIN_NUM_PHASES = 6
+};
+
+/* Fill *opt with the defaults listed above.  Never fails for a non-NULL opt. */
+LINMIN_API linmin_status linmin_default_options(linmin_options *opt);
+
+/*
+ * Create a handle for one reference library (Sec. 2.4/2.5: the mineral
+ * spectra plus any additional level/slope spectra, all as columns).
+ *   library  P x L float32 (see conventions), host or device, read during
+ *            the call only (the handle keeps a device copy);
+ *   L, P     1 <= P <= LINMIN_MAX_P, P <= L <= LINMIN_MAX_L;
+ *   opt      NULL for defaults;
+ *   out      receives the handle (NULL on failure).
+ * Returns LINMIN_ERR_RANK when rank [S^T; 1^T] < P (checked in fp64 on the
+ * host): the fully constrained minimiser is then not unique (Sec. 5: the
+ * constraints remove degeneracies only when this rank is full).
+ */
+LINMIN_API linmin_status linmin_create(const float *library, int L, int P,
+                            const linmin_options *opt, linmin_handle *out);
+
+/*
+ * Unmix N pixels: whitening (Sec. 2.3), projection c = S W^2 y,
+ * primal-dual interior-point FCLS per pixel (Sec. 2.2), extended precision
+ * KKT refinement on the support, abundance uncertainties (Sec. 2.3) and
+ * the RMS of the fit.
+ *   cube  N x L float32, host or device;  N >= 0 (N = 0 is a no-op);
+ *   sigma L float32 > 0, host or device;
+ *   outputs as in the conventions (NULL = skip).
+ * Device pointers: returns after queueing (use linmin_wait to learn about
+ * non-converged pixels).  Host pointers: synchronous; returns
+ * LINMIN_ERR_NOT_CONVERGED when some pixel has iterations < 0.
+ */
+LINMIN_API linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N,
+                           const float *sigma, float *abundances,
+                           float *uncertainties, float *residual_rms,
+                           int *iterations);
+
+/* Synchronise the handle's stream.  *n_not_converged (may be NULL) receives
+ * the number of pixels of the last linmin_unmix that hit max_iter.  Returns
+ * LINMIN_ERR_NOT_CONVERGED when that number is non-zero. */
+LINMIN_API linmin_status linmin_wait(linmin_handle h, long long *n_not_converged);
+
+/* Device time (ms) of each phase of the last linmin_unmix on h, measured
+ * with CUDA events on the handle's stream; requires opt.profile.  ms_out
+ * receives min(n, LINMIN_NUM_PHASES) values; synchronises the stream.
+ * Returns LINMIN_ERR_INVALID when profiling is off or nothing ran yet. */
+LINMIN_API linmin_status linmin_phase_times(linmin_handle h, float *ms_out, int n);
+
+/* Free the handle and its device memory (synchronises its stream first).
+ * NULL is accepted. */
+LINMIN_API linmin_status linmin_destroy(linmin_handle h);
+
+/* One-line description of the last error on h (or of the last failed
+ * linmin_create when h is NULL).  The string lives until the next call. */
+LINMIN_API const char *linmin_last_error(linmin_handle h);
+
+/* Library version string. */
+LINMIN_API const char *linmin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LINMIN_H */

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -34,12 +35,16 @@ MAX_ITER = 200
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable flags, no -march)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or \
+    stamp = os.path.join(_BUILD, "machine")
+    same_machine = os.path.exists(stamp) and open(stamp).read() == platform.machine()
+    if force or not same_machine or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread",
                                "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB_PATH
 
 

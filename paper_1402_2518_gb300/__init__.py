@@ -1,0 +1,9 @@
+"""LinMin fully constrained unmixing on GB300 (sm_103a).
+
+The product is the C-ABI library ``liblinmin.so`` (include/linmin.h) built
+from ``csrc/``; ``linmin`` is its ctypes binding.
+"""
+from .linmin import (EXPORTED, LinminError, Unmixer, library_path, linmin_create,  # noqa: F401
+                     linmin_default_options, linmin_destroy, linmin_last_error,
+                     linmin_options, linmin_phase_times, linmin_unmix, linmin_version,
+                     linmin_wait, load)

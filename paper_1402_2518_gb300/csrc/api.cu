@@ -1,0 +1,390 @@
+// C ABI of the LinMin library (see include/linmin.h for the contract).
+//
+// A call of linmin_unmix queues, on the handle's stream:
+//   1. library preparation for this sigma (fp64 Gram, scale, hi/lo splits);
+//   2. the double-float projection c~ = B~^T y + rho;
+//   3. the interior-point kernel, float32 residual phase, until mu <= mu_ref;
+//   4. the interior-point kernel, double-float residual phase, to the stop test;
+//   5. the fp64 support refinement (abundances, uncertainties);
+//   6. the RMS of the fit.
+// Host pointers are staged through handle-owned device buffers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ipm.cuh"
+#include "kernels.cuh"
+#include "linmin.h"
+
+using namespace lm;
+
+struct linmin_ctx {
+    int L = 0, P = 0;
+    Bucket bucket{};
+    linmin_options opt{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+
+    float *dS = nullptr;               // P x L library
+    Prep prep{};                       // per-sigma buffers
+    unsigned long long *dcnt = nullptr;// [0] phase-A counter, [1] phase-B counter,
+                                       // [2] not converged, [3] unverified refinements
+    // per-pixel scratch
+    long long capN = 0;
+    float *c_hi = nullptr, *c_lo = nullptr, *x = nullptr, *lam = nullptr, *nu = nullptr;
+    int *it = nullptr;
+    // host-pointer staging
+    long long capIO = 0;
+    float *io_cube = nullptr, *io_sigma = nullptr, *io_x = nullptr, *io_sx = nullptr,
+          *io_rms = nullptr;
+    int *io_it = nullptr;
+    // phase events (profile mode)
+    cudaEvent_t ev[LINMIN_NUM_PHASES + 1] = {};
+    bool timed = false;
+};
+
+static void mark(linmin_ctx *h, int i)
+{
+    if (h->opt.profile) cudaEventRecord(h->ev[i], h->stream);
+}
+
+static std::string g_create_error;
+static thread_local std::string g_msg;
+
+static linmin_status fail(linmin_ctx *h, linmin_status st, const std::string &m)
+{
+    if (h) h->err = m; else g_create_error = m;
+    return st;
+}
+
+static linmin_status cuda_fail(linmin_ctx *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LINMIN_ERR_OOM : LINMIN_ERR_CUDA, m);
+}
+
+#define LM_CUDA(h, call, what)                         \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return cuda_fail(h, _e, what); \
+    } while (0)
+
+// true when p is device (or managed) memory of this process
+static bool is_device_ptr(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t n)
+{
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+// rank [S^T; 1^T] == P in fp64 (modified Gram-Schmidt with one
+// re-orthogonalisation pass on the P columns of length L + 1)
+static bool full_rank(const std::vector<float> &S, int L, int P)
+{
+    const int n = L + 1;
+    std::vector<double> Q((size_t)P * n);
+    int r = 0;
+    for (int j = 0; j < P; ++j) {
+        std::vector<double> v(n);
+        for (int l = 0; l < L; ++l) v[l] = S[(size_t)j * L + l];
+        v[L] = 1.0;
+        double n0 = 0.0;
+        for (double e : v) n0 += e * e;
+        n0 = std::sqrt(n0);
+        if (n0 == 0.0) return false;
+        for (int pass = 0; pass < 2; ++pass)
+            for (int q = 0; q < r; ++q) {
+                double d = 0.0;
+                for (int l = 0; l < n; ++l) d += Q[(size_t)q * n + l] * v[l];
+                for (int l = 0; l < n; ++l) v[l] -= d * Q[(size_t)q * n + l];
+            }
+        double nv = 0.0;
+        for (double e : v) nv += e * e;
+        nv = std::sqrt(nv);
+        if (nv <= 1e-10 * n0) return false;
+        for (int l = 0; l < n; ++l) Q[(size_t)r * n + l] = v[l] / nv;
+        ++r;
+    }
+    return true;
+}
+
+extern "C" {
+
+const char *linmin_version(void) { return "linmin-gb300 0.1 (sm_103a)"; }
+
+linmin_status linmin_default_options(linmin_options *opt)
+{
+    if (!opt) return LINMIN_ERR_INVALID;
+    opt->precision = LINMIN_PROJ_DF;
+    opt->constraint = LINMIN_STO;
+    opt->max_iter = 100;
+    opt->tol = 1e-9f;
+    opt->refine_mu = 1e-9f;
+    opt->cuda_stream = nullptr;
+    opt->profile = 0;
+    return LINMIN_OK;
+}
+
+linmin_status linmin_create(const float *library, int L, int P, const linmin_options *opt,
+                            linmin_handle *out)
+{
+    if (!out) return fail(nullptr, LINMIN_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!library) return fail(nullptr, LINMIN_ERR_INVALID, "library is NULL");
+    if (P < 1 || P > LINMIN_MAX_P)
+        return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P must be in [1, LINMIN_MAX_P]");
+    if (L < P || L > LINMIN_MAX_L)
+        return fail(nullptr, LINMIN_ERR_INVALID, "L must be in [P, 4096]");
+    linmin_options o;
+    linmin_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != LINMIN_PROJ_DF || o.constraint != LINMIN_STO)
+        return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "only PROJ_DF and STO are built");
+    if (o.max_iter < 1 || !(o.tol > 0.f) || !(o.refine_mu > 0.f))
+        return fail(nullptr, LINMIN_ERR_INVALID, "max_iter >= 1, tol > 0, refine_mu > 0");
+
+    std::vector<float> hS((size_t)P * L);
+    const bool on_dev = is_device_ptr(library);
+    cudaError_t e = on_dev ? cudaMemcpy(hS.data(), library, hS.size() * 4, cudaMemcpyDeviceToHost)
+                           : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy library");
+    if (!on_dev) std::memcpy(hS.data(), library, hS.size() * 4);
+    for (float v : hS)
+        if (!std::isfinite(v)) return fail(nullptr, LINMIN_ERR_INVALID, "library has NaN/Inf");
+    if (!full_rank(hS, L, P))
+        return fail(nullptr, LINMIN_ERR_RANK,
+                    "rank [S^T; 1^T] < P: the constrained minimiser is not unique");
+
+    linmin_ctx *h = new linmin_ctx();
+    h->L = L; h->P = P; h->opt = o;
+    h->stream = (cudaStream_t)o.cuda_stream;
+    cudaGetDevice(&h->device);
+    if (!ipm_bucket(P, &h->bucket)) { delete h; return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P"); }
+    const int PP = h->bucket.PP, PQ = pq_of(P);
+    cudaError_t a = cudaSuccess;
+#define A(call) if (a == cudaSuccess) a = (call)
+    A(dalloc(&h->dS, (size_t)P * L));
+    A(dalloc(&h->prep.G64, (size_t)P * P));
+    A(dalloc(&h->prep.Gt64, (size_t)P * P));
+    A(dalloc(&h->prep.scale, 1));
+    A(dalloc(&h->prep.Ghi, (size_t)PP * PP));
+    A(dalloc(&h->prep.Glo, (size_t)PP * PP));
+    A(dalloc(&h->prep.grs, (size_t)PP));
+    A(dalloc(&h->prep.gdiag, (size_t)P));
+    A(dalloc(&h->prep.Bhi, (size_t)L * PQ));
+    A(dalloc(&h->prep.Blo, (size_t)L * PQ));
+    A(dalloc(&h->prep.flags, 1));
+    A(dalloc(&h->dcnt, 4));
+    A(cudaMemcpy(h->dS, hS.data(), hS.size() * 4, cudaMemcpyHostToDevice));
+    if (o.profile)
+        for (int i = 0; i <= LINMIN_NUM_PHASES; ++i) A(cudaEventCreate(&h->ev[i]));
+#undef A
+    if (a != cudaSuccess) {
+        linmin_status st = cuda_fail(nullptr, a, "linmin_create allocation");
+        linmin_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LINMIN_OK;
+}
+
+static linmin_status ensure_scratch(linmin_ctx *h, long long N)
+{
+    if (N <= h->capN) return LINMIN_OK;
+    const size_t np = (size_t)N * h->P;
+    cudaError_t a = cudaSuccess;
+#define A(call) if (a == cudaSuccess) a = (call)
+    A(dalloc(&h->c_hi, np));
+    A(dalloc(&h->c_lo, np));
+    A(dalloc(&h->x, np));
+    A(dalloc(&h->lam, np));
+    A(dalloc(&h->nu, (size_t)N));
+    A(dalloc(&h->it, (size_t)N));
+#undef A
+    if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
+    h->capN = N;
+    return LINMIN_OK;
+}
+
+static linmin_status ensure_io(linmin_ctx *h, long long N)
+{
+    if (N <= h->capIO) return LINMIN_OK;
+    const size_t np = (size_t)N * h->P;
+    cudaError_t a = cudaSuccess;
+#define A(call) if (a == cudaSuccess) a = (call)
+    A(dalloc(&h->io_cube, (size_t)N * h->L));
+    A(dalloc(&h->io_sigma, (size_t)h->L));
+    A(dalloc(&h->io_x, np));
+    A(dalloc(&h->io_sx, np));
+    A(dalloc(&h->io_rms, (size_t)N));
+    A(dalloc(&h->io_it, (size_t)N));
+#undef A
+    if (a != cudaSuccess) { h->capIO = 0; return cuda_fail(h, a, "staging allocation"); }
+    h->capIO = N;
+    return LINMIN_OK;
+}
+
+linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, const float *sigma,
+                           float *abundances, float *uncertainties, float *residual_rms,
+                           int *iterations)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    if (N < 0) return fail(h, LINMIN_ERR_INVALID, "N < 0");
+    if (N == 0) return LINMIN_OK;
+    if (!cube || !sigma) return fail(h, LINMIN_ERR_INVALID, "cube or sigma is NULL");
+    if (N > (1LL << 40)) return fail(h, LINMIN_ERR_INVALID, "N too large");
+    const int L = h->L, P = h->P;
+    cudaStream_t st = h->stream;
+    LM_CUDA(h, cudaSetDevice(h->device), "cudaSetDevice");
+
+    const bool dev_cube = is_device_ptr(cube), dev_sigma = is_device_ptr(sigma);
+    const bool dev_out[4] = {!abundances || is_device_ptr(abundances),
+                             !uncertainties || is_device_ptr(uncertainties),
+                             !residual_rms || is_device_ptr(residual_rms),
+                             !iterations || is_device_ptr(iterations)};
+    const bool host_any = !dev_cube || !dev_sigma || !dev_out[0] || !dev_out[1] || !dev_out[2] ||
+                          !dev_out[3];
+    if (!dev_sigma) {
+        for (int l = 0; l < L; ++l)
+            if (!(sigma[l] > 0.f) || !std::isfinite(sigma[l]))
+                return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
+    }
+    linmin_status s;
+    if ((s = ensure_scratch(h, N)) != LINMIN_OK) return s;
+    if (host_any && (s = ensure_io(h, N)) != LINMIN_OK) return s;
+
+    const size_t np = (size_t)N * P;
+    const float *d_cube = cube, *d_sigma = sigma;
+    if (!dev_cube) {
+        LM_CUDA(h, cudaMemcpyAsync(h->io_cube, cube, (size_t)N * L * 4, cudaMemcpyHostToDevice, st),
+                "copy cube");
+        d_cube = h->io_cube;
+    }
+    if (!dev_sigma) {
+        LM_CUDA(h, cudaMemcpyAsync(h->io_sigma, sigma, (size_t)L * 4, cudaMemcpyHostToDevice, st),
+                "copy sigma");
+        d_sigma = h->io_sigma;
+    }
+    float *d_x = abundances ? (dev_out[0] ? abundances : h->io_x) : h->x;
+    float *d_sx = uncertainties ? (dev_out[1] ? uncertainties : h->io_sx) : nullptr;
+    float *d_rms = residual_rms ? (dev_out[2] ? residual_rms : h->io_rms) : nullptr;
+    int *d_it = iterations ? (dev_out[3] ? iterations : h->io_it) : nullptr;
+
+    LM_CUDA(h, cudaMemsetAsync(h->prep.flags, 0, sizeof(int), st), "memset");
+    LM_CUDA(h, cudaMemsetAsync(h->dcnt, 0, 4 * sizeof(unsigned long long), st), "memset");
+    mark(h, 0);
+    LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
+    mark(h, 1);
+    LM_CUDA(h, launch_project(d_cube, N, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st),
+            "projection kernel");
+    mark(h, 2);
+
+    IpmArgs ia;
+    ia.N = N; ia.P = P; ia.max_iter = h->opt.max_iter;
+    ia.c_hi = h->c_hi; ia.c_lo = h->c_lo;
+    ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
+    ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
+    ia.n_notconv = h->dcnt + 2;
+    ia.mu_ref = h->opt.refine_mu; ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    ia.counter = h->dcnt + 0;
+    LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel (float32 residual)");
+    mark(h, 3);
+    ia.counter = h->dcnt + 1;
+    LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "interior-point kernel (double-float residual)");
+    mark(h, 4);
+
+    RefineArgs ra;
+    ra.N = N; ra.P = P; ra.Gt64 = h->prep.Gt64; ra.scale = h->prep.scale; ra.gdiag = h->prep.gdiag;
+    ra.c_hi = h->c_hi; ra.c_lo = h->c_lo; ra.x_in = h->x; ra.lam_in = h->lam;
+    ra.x_out = d_x; ra.sx_out = d_sx; ra.n_unverified = h->dcnt + 3;
+    ra.tol_x = 1e-9; ra.tol_g = 1e-9;
+    LM_CUDA(h, launch_refine(ra, st), "refinement kernel");
+    mark(h, 5);
+    if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
+    mark(h, 6);
+    h->timed = h->opt.profile != 0;
+    if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
+                      "copy iterations");
+
+    if (!host_any) return LINMIN_OK;
+    if (abundances && !dev_out[0])
+        LM_CUDA(h, cudaMemcpyAsync(abundances, d_x, np * 4, cudaMemcpyDeviceToHost, st), "copy x");
+    if (uncertainties && !dev_out[1])
+        LM_CUDA(h, cudaMemcpyAsync(uncertainties, d_sx, np * 4, cudaMemcpyDeviceToHost, st), "copy sx");
+    if (residual_rms && !dev_out[2])
+        LM_CUDA(h, cudaMemcpyAsync(residual_rms, d_rms, (size_t)N * 4, cudaMemcpyDeviceToHost, st),
+                "copy rms");
+    if (iterations && !dev_out[3])
+        LM_CUDA(h, cudaMemcpyAsync(iterations, d_it, (size_t)N * 4, cudaMemcpyDeviceToHost, st),
+                "copy iterations");
+    return linmin_wait(h, nullptr);
+}
+
+linmin_status linmin_wait(linmin_handle h, long long *n_not_converged)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    unsigned long long c[4] = {0, 0, 0, 0};
+    int flags = 0;
+    LM_CUDA(h, cudaStreamSynchronize(h->stream), "kernel execution");
+    LM_CUDA(h, cudaMemcpy(c, h->dcnt, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    LM_CUDA(h, cudaMemcpy(&flags, h->prep.flags, sizeof(int), cudaMemcpyDeviceToHost), "read flags");
+    if (n_not_converged) *n_not_converged = (long long)c[2];
+    if (flags & 1) return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
+    if (flags & 2) return fail(h, LINMIN_ERR_INVALID, "library has a zero whitened scale");
+    if (c[2]) return fail(h, LINMIN_ERR_NOT_CONVERGED,
+                          std::to_string(c[2]) + " pixels hit max_iter");
+    return LINMIN_OK;
+}
+
+linmin_status linmin_phase_times(linmin_handle h, float *ms_out, int n)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    if (!h->opt.profile || !h->timed || !ms_out)
+        return fail(h, LINMIN_ERR_INVALID, "profiling is off or nothing was timed");
+    LM_CUDA(h, cudaEventSynchronize(h->ev[LINMIN_NUM_PHASES]), "event sync");
+    for (int i = 0; i < n && i < LINMIN_NUM_PHASES; ++i) {
+        float ms = 0.f;
+        LM_CUDA(h, cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]), "event time");
+        ms_out[i] = ms;
+    }
+    return LINMIN_OK;
+}
+
+linmin_status linmin_destroy(linmin_handle h)
+{
+    if (!h) return LINMIN_OK;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev)
+        if (e) cudaEventDestroy(e);
+    void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
+                    h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
+                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->io_cube, h->io_sigma,
+                    h->io_x, h->io_sx, h->io_rms, h->io_it};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete h;
+    return LINMIN_OK;
+}
+
+const char *linmin_last_error(linmin_handle h)
+{
+    g_msg = h ? h->err : g_create_error;
+    return g_msg.c_str();
+}
+
+}  // extern "C"

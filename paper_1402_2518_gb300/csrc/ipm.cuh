@@ -1,0 +1,474 @@
+// Batched primal-dual interior-point FCLS solve (IPLS, Sec. 2.2) on sm_103a.
+//
+// Problem per pixel, in the scaled units set by the library preparation
+// (G~ = G / s + rho 1 1^T, c~ = c / s + rho 1, s = trace(G) / P, rho = 1):
+//
+//     minimise 1/2 x^T G~ x - c~^T x   s.t.  x >= 0,  1^T x = 1
+//
+// Adding rho 1 1^T to G and rho 1 to c changes nothing on the feasible set
+// (the added term rho/2 (1^T x - 1)^2 vanishes there), so the minimiser is
+// the FCLS one of eqs. NonNegativity/SumToOne; it makes every barrier
+// Hessian H = G~ + X^-1 Lambda positive definite when rank [S^T; 1^T] = P
+// even though G itself is singular for the level/slope spectra of Sec. 2.5
+// (flat, increasing and decreasing slopes are linearly dependent).
+//
+// Each Newton step solves the bordered KKT system
+//     [ H   1 ] [dx ]   [ -r_d - X^-1 r_c ]
+//     [ 1^T 0 ] [dnu] = [ -r_p            ]
+// through H = L L^T and u = H^-1 1: dnu = (1^T H^-1 r + r_p) / (1^T u),
+// dx = H^-1 (r - dnu 1); only forward solves are needed for the scalars
+// (1^T H^-1 r = (L^-1 1).(L^-1 r)), one back solve per direction.  The
+// step is Mehrotra's predictor-corrector with a common primal/dual step
+// length (fraction to the boundary eta).
+//
+// Mapping: a group of G consecutive lanes owns one pixel; lane t owns rows
+// i = s*G + t (slot s < NS) of the lower triangle of H, kept in registers
+// (row length (s+1)*G, fully unrolled, compile-time indices).  The
+// right-looking factorisation broadcasts column k through shared memory
+// (all columns are kept: they serve the back solves), the right-hand sides
+// 1 and r_aff are eliminated during the factorisation (forward solves for
+// free).  Groups take pixels from a global work counter and refill as soon
+// as their pixel leaves the active set (converged pixels are compacted out
+// of the running set; warps run while any group has work).
+//
+// Two instantiations per size: ACC = false iterates with the float32 KKT
+// residual until mu <= mu_ref and saves the state; ACC = true continues with
+// the residual G~ x - c~ evaluated in double-float (G~ and c~ as hi+lo
+// float32 pairs) until the stopping test, so the iterates converge to the
+// minimiser of the exact data rather than of its float32 rounding.
+#pragma once
+#include "common.cuh"
+
+namespace lm {
+
+constexpr int IPM_WARPS = 4;
+
+// Compiler-only memory fence: keeps the scheduler from hoisting the shared
+// memory loads of later unrolled steps (which would hold them all in
+// registers at once).
+#define LM_STEP_FENCE() asm volatile("" ::: "memory")
+constexpr int IPM_THREADS = IPM_WARPS * 32;
+
+struct IpmArgs {
+    long long N;
+    int P;
+    int max_iter;
+    const float *c_hi, *c_lo;      // N x P, scaled projection c~ (hi + lo)
+    const float *Ghi, *Glo;        // PP x PP row-major, zero padded (G~ hi + lo)
+    const float *grs;              // PP: G~ (1/P) 1, the gradient term at x0 = 1/P
+    float *x_state, *lam_state;    // N x P
+    float *nu_state;               // N
+    int *it_state;                 // N: iterations so far (phase A) / final (phase B, <0: cap)
+    unsigned long long *counter;   // pixel work counter, zeroed before the launch
+    unsigned long long *n_notconv; // phase B: number of pixels that hit max_iter
+    float mu_ref, tol_c, tol_d, eta;
+};
+
+template <int NS_, int G_>
+struct IpmCfg {
+    static constexpr int NS = NS_, G = G_;
+    static constexpr int PP = NS * G;      // padded size, multiple of 4
+    static constexpr int GPW = 32 / G;     // pixel groups per warp
+    // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
+    static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
+    static constexpr __host__ __device__ int collen(int k) { return PP - alignrow(k); }
+    static constexpr __host__ __device__ int colstart(int k) {
+        int s = 0;
+        for (int q = 0; q < k; ++q) s += collen(q);
+        return s;
+    }
+    static constexpr int LBUF = colstart(PP);
+    // per-group floats: L columns + x broadcast; stride = 4 (mod 32) words
+    // so that the GPW groups of a warp hit distinct banks with LDS.128
+    static constexpr int GROUP_RAW = LBUF + PP;
+    static constexpr int GROUP_FLOATS = ((GROUP_RAW + 31) / 32) * 32 + 4;
+    static constexpr size_t smem_bytes(bool acc) {
+        return sizeof(float) * ((acc ? 2 : 1) * PP * PP + PP +
+                                (size_t)IPM_WARPS * GPW * GROUP_FLOATS);
+    }
+};
+
+template <int NS, int G, bool ACC>
+__global__ void __launch_bounds__(IPM_THREADS)
+ipm_kernel(const IpmArgs a)
+{
+    using C = IpmCfg<NS, G>;
+    constexpr int PP = C::PP;
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr float TINY = 1e-30f, BIGPIV = 1e30f, DMAX = 1e30f;
+
+    extern __shared__ __align__(16) float sm[];
+    float *sGhi = sm;
+    float *sGlo = sm + PP * PP;                      // only with ACC
+    float *sGrs = sm + (ACC ? 2 : 1) * PP * PP;
+    float *grp0 = sGrs + PP;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = lane % G, gid = lane / G;
+    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (gid * G));
+    float *colbuf = grp0 + (warp * C::GPW + gid) * C::GROUP_FLOATS;
+    float *xbuf = colbuf + C::LBUF;
+
+    for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+        sGhi[e] = a.Ghi[e];
+        if (ACC) sGlo[e] = a.Glo[e];
+    }
+    for (int e = threadIdx.x; e < PP; e += blockDim.x) sGrs[e] = a.grs[e];
+    __syncthreads();
+
+    const int P = a.P;
+    const float invP = 1.0f / (float)P;
+    bool valid[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) valid[s] = s * G + t < P;
+
+    float x[NS], lam[NS], nu = 0.f;
+    int it = 0;
+    size_t cbase = 0;   // offset of the current pixel in the N x P arrays
+
+    auto fetch = [&]() -> long long {
+        unsigned long long v = 0;
+        if (t == 0) v = atomicAdd(a.counter, 1ULL);
+        v = __shfl_sync(gmask, v, 0, G);
+        return (long long)v;
+    };
+
+    // load c~ and either the start point (phase A) or the saved state (B)
+    auto load_pixel = [&](long long p) {
+        const size_t base = (size_t)p * P;
+        cbase = base;
+        if (!ACC) {
+            // x0 = 1/P; g0 = G~ x0 - c~; nu0 makes lambda0 = g0 + nu0 >= delta
+            float gmin = 3.4e38f, gmax = -3.4e38f, g0[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                g0[s] = valid[s] ? sGrs[s * G + t] - __ldg(a.c_hi + base + s * G + t) : 0.f;
+                if (valid[s]) { gmin = fminf(gmin, g0[s]); gmax = fmaxf(gmax, g0[s]); }
+            }
+            for (int off = 1; off < G; off <<= 1) {
+                gmin = fminf(gmin, __shfl_xor_sync(gmask, gmin, off));
+                gmax = fmaxf(gmax, __shfl_xor_sync(gmask, gmax, off));
+            }
+            const float delta = (gmax - gmin) + 1e-3f;
+            nu = delta - gmin;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                x[s] = valid[s] ? invP : 0.f;
+                lam[s] = valid[s] ? g0[s] + nu : 0.f;
+            }
+            it = 0;
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int i = s * G + t;
+                x[s] = valid[s] ? a.x_state[base + i] : 0.f;
+                lam[s] = valid[s] ? a.lam_state[base + i] : 0.f;
+            }
+            nu = a.nu_state[p];
+            it = a.it_state[p];
+        }
+    };
+
+    long long pix = fetch();
+    bool alive = pix < a.N;
+    if (alive) load_pixel(pix);
+    else {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) { x[s] = valid[s] ? invP : 0.f; lam[s] = valid[s] ? 1.f : 0.f; }
+    }
+
+    float rd[NS];
+    float rp = 0.f, mu = 0.f, rdmax = 0.f, dec = 0.f;
+
+    // r_d = G~ x - c~ - lambda + nu 1 and the scalar measures (group-uniform)
+    auto residual = [&]() {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) xbuf[s * G + t] = x[s];
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int i = s * G + t;
+            const float *grow = sGhi + i * PP;
+            float gx;
+            if (!ACC) {
+                float acc = 0.f;
+#pragma unroll
+                for (int j4 = 0; j4 < PP / 4; ++j4) {
+                    const float4 g = *reinterpret_cast<const float4 *>(grow + 4 * j4);
+                    const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
+                    acc = fmaf(g.x, xv.x, acc);
+                    acc = fmaf(g.y, xv.y, acc);
+                    acc = fmaf(g.z, xv.z, acc);
+                    acc = fmaf(g.w, xv.w, acc);
+                }
+                gx = acc - (valid[s] ? __ldg(a.c_hi + cbase + i) : 0.f);
+            } else {
+                const float *glow = sGlo + i * PP;
+                dot2 d;
+#pragma unroll
+                for (int j4 = 0; j4 < PP / 4; ++j4) {
+                    const float4 g = *reinterpret_cast<const float4 *>(grow + 4 * j4);
+                    const float4 gl = *reinterpret_cast<const float4 *>(glow + 4 * j4);
+                    const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
+                    d.add_prod(g.x, xv.x); d.c = fmaf(gl.x, xv.x, d.c);
+                    d.add_prod(g.y, xv.y); d.c = fmaf(gl.y, xv.y, d.c);
+                    d.add_prod(g.z, xv.z); d.c = fmaf(gl.z, xv.z, d.c);
+                    d.add_prod(g.w, xv.w); d.c = fmaf(gl.w, xv.w, d.c);
+                }
+                if (valid[s]) d.add_df(df{-__ldg(a.c_hi + cbase + i), -__ldg(a.c_lo + cbase + i)});
+                const df r = d.result();
+                gx = r.hi + r.lo;
+            }
+            rd[s] = valid[s] ? (gx - lam[s]) + nu : 0.f;
+            LM_STEP_FENCE();
+        }
+        __syncwarp();
+        float sx = 0.f, sxl = 0.f, rmax = 0.f, dmx = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            sx += x[s];
+            sxl = fmaf(x[s], lam[s], sxl);
+            rmax = fmaxf(rmax, fabsf(rd[s]));
+            if (valid[s]) dmx = fmaxf(dmx, fminf(x[s], lam[s]));
+        }
+        rp = group_sum(sx, G) - 1.0f;
+        mu = group_sum(sxl, G) * invP;
+        rdmax = group_max(rmax, G);
+        dec = group_max(dmx, G);
+    };
+
+    while (__any_sync(FULL, alive)) {
+        residual();
+
+        // ---- leave the active set / refill (per group)
+        bool done;
+        if (!ACC) done = (mu <= a.mu_ref) || (it >= a.max_iter);
+        else done = ((rdmax <= a.tol_d) && (dec <= a.tol_c)) || (it >= a.max_iter);
+        done = done && alive;
+        if (__any_sync(FULL, done)) {
+            if (done) {
+                const size_t base = (size_t)pix * P;
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const int i = s * G + t;
+                    if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
+                }
+                const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
+                if (t == 0) {
+                    a.nu_state[pix] = nu;
+                    if (!ACC) a.it_state[pix] = it;
+                    else {
+                        a.it_state[pix] = conv ? it : -it;
+                        if (!conv) atomicAdd(a.n_notconv, 1ULL);
+                    }
+                }
+                pix = fetch();
+                alive = pix < a.N;
+                if (alive) load_pixel(pix);
+            }
+            residual();
+        }
+        if (!__any_sync(FULL, alive)) break;
+
+        // ---- barrier Hessian H = G~ + diag(lambda / x), lower rows in registers
+        float H[NS][PP];
+        auto Dof = [&](int s) -> float { return valid[s] ? fminf(lam[s] / x[s], DMAX) : 1.f; };
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int i = s * G + t;
+            const float Ds = Dof(s);
+            const float *grow = sGhi + i * PP;
+#pragma unroll
+            for (int j4 = 0; j4 < (s + 1) * G / 4; ++j4) {
+                const float4 g = *reinterpret_cast<const float4 *>(grow + 4 * j4);
+                H[s][4 * j4 + 0] = g.x; H[s][4 * j4 + 1] = g.y;
+                H[s][4 * j4 + 2] = g.z; H[s][4 * j4 + 3] = g.w;
+            }
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const int j = s * G + q;
+                if (!valid[s]) H[s][j] = (q == t) ? 1.f : 0.f;
+                else if (q == t) H[s][j] += Ds;
+            }
+            if (!valid[s]) {
+#pragma unroll
+                for (int j = 0; j < s * G; ++j) H[s][j] = 0.f;
+            }
+        }
+
+        // ---- factorise H = L L^T; eliminate rhs B1 = 1, B2 = r_aff = -r_d - lambda
+        float B1[NS], B2[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            B1[s] = valid[s] ? 1.f : 0.f;
+            B2[s] = -rd[s] - lam[s];
+        }
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            const int sk = k / G, tk = k % G;
+            float d = __shfl_sync(FULL, H[sk][k], tk, G);
+            d = (d > TINY) ? d : BIGPIV;
+            const float r = rsqrtf(d);
+#pragma unroll
+            for (int s = sk; s < NS; ++s) {
+                const bool below = (s > sk) || (t > tk);
+                if (below) {
+                    H[s][k] *= r;
+                    colbuf[C::colstart(k) + s * G + t - C::alignrow(k)] = H[s][k];
+                }
+            }
+            float z1 = 0.f, z2 = 0.f;
+            if (t == tk) {
+                H[sk][k] = r;                 // keep 1 / L_kk on the diagonal
+                z1 = B1[sk] * r; z2 = B2[sk] * r;
+                B1[sk] = z1; B2[sk] = z2;
+            }
+            __syncwarp();
+            z1 = __shfl_sync(FULL, z1, tk, G);
+            z2 = __shfl_sync(FULL, z2, tk, G);
+            if (k + 1 < PP) {
+                float lik[NS];
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const bool below = (s > sk) || (t > tk);
+                    lik[s] = (s >= sk && below) ? H[s][k] : 0.f;
+                }
+#pragma unroll
+                for (int j4 = C::alignrow(k) / 4; j4 < PP / 4; ++j4) {
+                    const float4 lv = *reinterpret_cast<const float4 *>(
+                        colbuf + C::colstart(k) + 4 * j4 - C::alignrow(k));
+                    const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = 4 * j4 + q;
+                        if (j <= k) continue;
+#pragma unroll
+                        for (int s = sk; s < NS; ++s)
+                            if (j < (s + 1) * G) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
+                    }
+                }
+#pragma unroll
+                for (int s = sk; s < NS; ++s) {
+                    B1[s] = fmaf(-lik[s], z1, B1[s]);
+                    B2[s] = fmaf(-lik[s], z2, B2[s]);
+                }
+            }
+            LM_STEP_FENCE();
+        }
+        __syncwarp();
+
+        // back solve L^T w = v in place (v distributed by rows); uses the
+        // stored columns of L and 1/L_kk on each owner's diagonal
+        auto back_solve = [&](float (&v)[NS]) {
+            // the loads of step k take their address from the value
+            // broadcast at step k+1 ((w == w) is 0 unless NaN), so the
+            // scheduler prefetches one step ahead instead of hoisting the
+            // loads of every step (which spills registers)
+            int dep = 0;
+#pragma unroll
+            for (int k = PP - 1; k >= 0; --k) {
+                const int sk = k / G, tk = k % G;
+                float lk[NS];
+#pragma unroll
+                for (int s = 0; s <= sk; ++s) {
+                    const int i = s * G + t;
+                    lk[s] = colbuf[C::colstart(i) - C::alignrow(i) + k + dep];
+                }
+                float w = 0.f;
+                if (t == tk) { w = v[sk] * H[sk][k]; v[sk] = w; }
+                w = __shfl_sync(FULL, w, tk, G);
+                dep = (w == w) ? 0 : 1;
+#pragma unroll
+                for (int s = 0; s <= sk; ++s) {
+                    const bool above = (s < sk) || (t < tk);
+                    if (above) v[s] = fmaf(-lk[s], w, v[s]);
+                }
+            }
+        };
+        // forward solve L z = b in place with the register rows of L
+        auto fwd_solve = [&](float (&b)[NS]) {
+#pragma unroll
+            for (int k = 0; k < PP; ++k) {
+                const int sk = k / G, tk = k % G;
+                float z = 0.f;
+                if (t == tk) { z = b[sk] * H[sk][k]; b[sk] = z; }
+                z = __shfl_sync(FULL, z, tk, G);
+#pragma unroll
+                for (int s = sk; s < NS; ++s) {
+                    const bool below = (s > sk) || (t > tk);
+                    if (below) b[s] = fmaf(-H[s][k], z, b[s]);
+                }
+                LM_STEP_FENCE();
+            }
+        };
+
+        // ---- predictor (affine scaling direction)
+        float p11 = 0.f, p1a = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) { p11 = fmaf(B1[s], B1[s], p11); p1a = fmaf(B1[s], B2[s], p1a); }
+        const float a11 = group_sum(p11, G);
+        const float a1a = group_sum(p1a, G);
+        const float dnu_a = (a1a + rp) / a11;
+        float dxa[NS], dla[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) dxa[s] = fmaf(-dnu_a, B1[s], B2[s]);
+        back_solve(dxa);
+        float ap = 1.f, ad = 1.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            dla[s] = valid[s] ? fmaf(-Dof(s), dxa[s], -lam[s]) : 0.f;
+            if (valid[s] && dxa[s] < 0.f) ap = fminf(ap, -x[s] / dxa[s]);
+            if (valid[s] && dla[s] < 0.f) ad = fminf(ad, -lam[s] / dla[s]);
+        }
+        ap = group_min(ap, G);
+        ad = group_min(ad, G);
+        float pma = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) pma = fmaf(fmaf(ap, dxa[s], x[s]), fmaf(ad, dla[s], lam[s]), pma);
+        const float mua = group_sum(pma, G) * invP;
+        float sig = (mu > 0.f) ? mua / mu : 0.f;
+        sig = fminf(sig * sig * sig, 1.f);
+        const float smu = sig * mu;
+
+        // ---- corrector: rhs -X^-1 (dx_aff o dlam_aff - sigma mu 1)
+        float corr[NS], zc[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            corr[s] = valid[s] ? fmaf(dxa[s], dla[s], -smu) / x[s] : 0.f;
+            zc[s] = -corr[s];
+        }
+        fwd_solve(zc);
+        float p1c = 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) p1c = fmaf(B1[s], zc[s], p1c);
+        const float dnu_c = group_sum(p1c, G) / a11;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) zc[s] = fmaf(-dnu_c, B1[s], zc[s]);
+        back_solve(zc);
+
+        float dx[NS], dl[NS];
+        ap = 1.f; ad = 1.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            dx[s] = dxa[s] + zc[s];
+            dl[s] = valid[s] ? fmaf(-Dof(s), dx[s], -lam[s] - corr[s]) : 0.f;
+            if (valid[s] && dx[s] < 0.f) ap = fminf(ap, -x[s] / dx[s]);
+            if (valid[s] && dl[s] < 0.f) ad = fminf(ad, -lam[s] / dl[s]);
+        }
+        ap = group_min(ap, G);
+        ad = group_min(ad, G);
+        const float alpha = fminf(1.f, a.eta * fminf(ap, ad));
+        const float dnu = dnu_a + dnu_c;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (valid[s]) {
+                x[s] = fmaxf(fmaf(alpha, dx[s], x[s]), TINY);
+                lam[s] = fmaxf(fmaf(alpha, dl[s], lam[s]), TINY);
+            }
+        }
+        nu = fmaf(alpha, dnu, nu);
+        ++it;
+    }
+}
+
+}  // namespace lm

@@ -1,0 +1,213 @@
+"""ctypes binding of liblinmin.so (C ABI in include/linmin.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name; all arithmetic runs in the library's CUDA kernels.  Arrays
+may be torch tensors (CUDA or CPU) or numpy arrays (host); they must be
+contiguous float32 (int32 for ``iterations``).  There is no CPU fallback:
+importing this module fails when the library cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+LINMIN_OK = 0
+LINMIN_ERR_INVALID = 1
+LINMIN_ERR_OOM = 2
+LINMIN_ERR_CUDA = 3
+LINMIN_ERR_RANK = 4
+LINMIN_ERR_TIMEOUT = 5
+LINMIN_ERR_NOT_CONVERGED = 6
+LINMIN_ERR_UNSUPPORTED = 7
+LINMIN_PROJ_DF = 0
+LINMIN_STO = 0
+LINMIN_MAX_P = 48
+LINMIN_MAX_L = 4096
+
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_RANK",
+                5: "ERR_TIMEOUT", 6: "ERR_NOT_CONVERGED", 7: "ERR_UNSUPPORTED"}
+
+EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_wait",
+            "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version")
+PHASES = ("prep", "project", "ipm_f32", "ipm_df", "refine", "rms")
+
+
+class linmin_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("constraint", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("tol", ctypes.c_float),
+                ("refine_mu", ctypes.c_float), ("cuda_stream", ctypes.c_void_p),
+                ("profile", ctypes.c_int)]
+
+
+class LinminError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load liblinmin.so (building it in-tree first if it is missing)."""
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError(f"{path} not built")
+        path = _build.build()
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    P = ctypes.c_void_p
+    lib.linmin_default_options.argtypes = [ctypes.POINTER(linmin_options)]
+    lib.linmin_default_options.restype = ctypes.c_int
+    lib.linmin_create.argtypes = [P, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(linmin_options), ctypes.POINTER(H)]
+    lib.linmin_create.restype = ctypes.c_int
+    lib.linmin_unmix.argtypes = [H, P, ctypes.c_longlong, P, P, P, P, P]
+    lib.linmin_unmix.restype = ctypes.c_int
+    lib.linmin_wait.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
+    lib.linmin_wait.restype = ctypes.c_int
+    lib.linmin_phase_times.argtypes = [H, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
+    lib.linmin_phase_times.restype = ctypes.c_int
+    lib.linmin_destroy.argtypes = [H]
+    lib.linmin_destroy.restype = ctypes.c_int
+    lib.linmin_last_error.argtypes = [H]
+    lib.linmin_last_error.restype = ctypes.c_char_p
+    lib.linmin_version.argtypes = []
+    lib.linmin_version.restype = ctypes.c_char_p
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load()
+    return _LIB
+
+
+def _ptr(a, dtype_name: str = "float32"):
+    """Raw pointer of a contiguous torch tensor / numpy array (or None)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):          # torch.Tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(a.dtype).split(".")[-1] != dtype_name:
+            raise TypeError(f"expected {dtype_name}, got {a.dtype}")
+        return ctypes.c_void_p(a.data_ptr())
+    if hasattr(a, "ctypes"):            # numpy.ndarray
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype.name != dtype_name:
+            raise TypeError(f"expected {dtype_name}, got {a.dtype}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(status: int, handle=None):
+    if status != LINMIN_OK:
+        raise LinminError(status, linmin_last_error(handle))
+    return status
+
+
+def linmin_default_options() -> linmin_options:
+    o = linmin_options()
+    _check(lib().linmin_default_options(ctypes.byref(o)))
+    return o
+
+
+def linmin_create(library, L: int, P: int, opt: linmin_options | None = None) -> ctypes.c_void_p:
+    """Handle for a P x L float32 library (host or device)."""
+    h = ctypes.c_void_p()
+    st = lib().linmin_create(_ptr(library), int(L), int(P),
+                             ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    _check(st, None)
+    return h
+
+
+def linmin_unmix(h, cube, N: int, sigma, abundances=None, uncertainties=None,
+                 residual_rms=None, iterations=None, check: bool = True) -> int:
+    st = lib().linmin_unmix(h, _ptr(cube), int(N), _ptr(sigma), _ptr(abundances),
+                            _ptr(uncertainties), _ptr(residual_rms),
+                            _ptr(iterations, "int32"))
+    if check and st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st
+
+
+def linmin_wait(h) -> tuple[int, int]:
+    n = ctypes.c_longlong(0)
+    st = lib().linmin_wait(h, ctypes.byref(n))
+    return st, int(n.value)
+
+
+def linmin_phase_times(h) -> dict:
+    """Per-phase device milliseconds of the last linmin_unmix (profile mode)."""
+    arr = (ctypes.c_float * len(PHASES))()
+    _check(lib().linmin_phase_times(h, arr, len(PHASES)), h)
+    return {k: float(v) for k, v in zip(PHASES, arr)}
+
+
+def linmin_destroy(h) -> int:
+    return lib().linmin_destroy(h)
+
+
+def linmin_last_error(h=None) -> str:
+    s = lib().linmin_last_error(h)
+    return s.decode() if s else ""
+
+
+def linmin_version() -> str:
+    return lib().linmin_version().decode()
+
+
+class Unmixer:
+    """Convenience owner of a handle; outputs are allocated as torch tensors
+    on the device of the inputs (plumbing only)."""
+
+    def __init__(self, library, max_iter: int = 100, tol: float = 1e-9,
+                 refine_mu: float = 1e-9, stream=None, profile: bool = False):
+        import torch
+        S = library if hasattr(library, "data_ptr") else torch.as_tensor(library)
+        S = S.to(torch.float32).contiguous()
+        self.P, self.L = int(S.shape[0]), int(S.shape[1])
+        opt = linmin_default_options()
+        opt.max_iter, opt.tol, opt.refine_mu = int(max_iter), float(tol), float(refine_mu)
+        opt.profile = int(bool(profile))
+        if stream is not None:
+            opt.cuda_stream = ctypes.c_void_p(int(stream.cuda_stream))
+        self.h = linmin_create(S, self.L, self.P, opt)
+
+    def __call__(self, cube, sigma):
+        import torch
+        N = int(cube.shape[0])
+        dev = cube.device
+        x = torch.empty((N, self.P), dtype=torch.float32, device=dev)
+        sx = torch.empty((N, self.P), dtype=torch.float32, device=dev)
+        rms = torch.empty((N,), dtype=torch.float32, device=dev)
+        it = torch.empty((N,), dtype=torch.int32, device=dev)
+        linmin_unmix(self.h, cube, N, sigma, x, sx, rms, it)
+        return x, sx, rms, it
+
+    def wait(self):
+        return linmin_wait(self.h)
+
+    def phase_times(self):
+        return linmin_phase_times(self.h)
+
+    def close(self):
+        if self.h:
+            linmin_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

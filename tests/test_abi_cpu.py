@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every symbol the header declares, and the binding's constants match
+the header."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1402_2518_gb300 as pkg
+from paper_1402_2518_gb300 import linmin
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "linmin.h")
+
+
+def _declared_functions():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"LINMIN_API\s+[\w\s\*]+?\b(linmin_\w+)\s*\(", txt)))
+
+
+def test_library_loads_and_exports_header_symbols():
+    lib = pkg.load()
+    declared = _declared_functions()
+    assert declared, "no declarations found in include/linmin.h"
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared but not exported"
+    assert sorted(linmin.EXPORTED) == declared
+
+
+def test_no_other_exports():
+    """Only the C ABI is visible (static CUDA runtime, hidden internals)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", linmin.library_path()],
+                         capture_output=True, text=True).stdout
+    syms = [l.split()[-1] for l in out.splitlines() if " T " in l]
+    assert sorted(syms) == sorted(linmin.EXPORTED), syms
+
+
+def test_header_constants_match_binding():
+    txt = open(HEADER).read()
+    for name in ("LINMIN_OK", "LINMIN_ERR_INVALID", "LINMIN_ERR_OOM", "LINMIN_ERR_CUDA",
+                 "LINMIN_ERR_RANK", "LINMIN_ERR_TIMEOUT", "LINMIN_ERR_NOT_CONVERGED",
+                 "LINMIN_ERR_UNSUPPORTED"):
+        m = re.search(rf"{name}\s*=\s*(\d+)", txt)
+        assert m and int(m.group(1)) == getattr(linmin, name)
+    for name in ("LINMIN_MAX_P", "LINMIN_MAX_L"):
+        m = re.search(rf"#define {name} (\d+)", txt)
+        assert m and int(m.group(1)) == getattr(linmin, name)
+
+
+def test_options_struct_layout_and_defaults():
+    o = pkg.linmin_default_options()
+    assert ctypes.sizeof(linmin.linmin_options) == 40
+    assert o.max_iter == 100 and abs(o.tol - 1e-9) < 1e-15 and abs(o.refine_mu - 1e-9) < 1e-15
+    assert o.precision == linmin.LINMIN_PROJ_DF and o.constraint == linmin.LINMIN_STO
+
+
+def test_invalid_arguments_rejected_on_host():
+    """Errors detected before any device work: no GPU is touched."""
+    import numpy as np
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    S = np.ones((4, 16), dtype=np.float32)
+    assert lib.linmin_create(None, 16, 4, None, ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, 0, None,
+                             ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
+    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, 49, None,
+                             ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
+    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 3, 4, None,
+                             ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
+    # four identical spectra: rank [S^T; 1^T] = 1 < 4
+    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, 4, None,
+                             ctypes.byref(h)) == linmin.LINMIN_ERR_RANK
+    assert "rank" in pkg.linmin_last_error(None)
+    bad = pkg.linmin_default_options()
+    bad.max_iter = 0
+    S2 = np.random.default_rng(0).uniform(0.2, 0.6, (4, 16)).astype(np.float32)
+    assert lib.linmin_create(S2.ctypes.data_as(ctypes.c_void_p), 16, 4, ctypes.byref(bad),
+                             ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_unmix(None, None, 0, None, None, None, None, None) == \
+        linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_destroy(None) == linmin.LINMIN_OK
+
+
+def test_binding_rejects_wrong_dtypes():
+    import numpy as np
+    with pytest.raises(TypeError):
+        pkg.linmin_create(np.ones((4, 16)), 16, 4)          # float64
+    with pytest.raises(ValueError):
+        pkg.linmin_create(np.ones((16, 4), np.float32).T, 16, 4)  # not contiguous
