@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--pixels", type=int, default=0,
+                    help="use only the first PIXELS pixels (small profiling case)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
     return ap.parse_args()
 
 
@@ -133,6 +136,32 @@ def cpu_baseline(cube, target_s: float):
             "sample": f"first {n} of {cube.N} pixels of {SPEC.name}, {dt:.1f} s"}
 
 
+def run_e2e(pkg, cube, steps):
+    """Seconds per step of linmin_unmix on pinned host buffers: the cube and
+    sigma are copied in and every output copied back inside the call."""
+    import torch
+    N, P, L = cube.N, cube.P, cube.L
+    Xh = torch.from_numpy(cube.X).pin_memory()
+    sgh = torch.from_numpy(cube.sigma).pin_memory()
+    xh = torch.empty((N, P)).pin_memory()
+    sxh = torch.empty((N, P)).pin_memory()
+    rh = torch.empty((N,)).pin_memory()
+    ih = torch.empty((N,), dtype=torch.int32).pin_memory()
+    h = pkg.linmin_create(cube.S, L, P)
+
+    def step():
+        pkg.linmin_unmix(h, Xh.numpy(), N, sgh.numpy(), xh.numpy(), sxh.numpy(),
+                         rh.numpy(), ih.numpy())
+
+    step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    pkg.linmin_destroy(h)
+    return dt
+
+
 def run_reference(args, cube):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -165,7 +194,7 @@ def run_reference(args, cube):
 def main():
     args = parse()
     ws, rank, local = dist_env()
-    cube = synth.make_cube(SPEC)
+    cube = synth.make_cube(SPEC, n_pix=args.pixels or None)
     if args.impl == "reference":
         run_reference(args, cube)
         return
@@ -227,27 +256,16 @@ def main():
     st, nbad = um.wait()
 
     # end to end through the C ABI with host buffers (pinned), copies inside
-    Xh = torch.from_numpy(cube.X).pin_memory()
-    sgh = torch.from_numpy(cube.sigma).pin_memory()
-    xh = torch.empty((N, P)).pin_memory(); sxh = torch.empty((N, P)).pin_memory()
-    rh = torch.empty((N,)).pin_memory(); ih = torch.empty((N,), dtype=torch.int32).pin_memory()
-    h_host = pkg.linmin_create(cube.S, L, P)
-
-    def step_host():
-        pkg.linmin_unmix(h_host, Xh.numpy(), N, sgh.numpy(), xh.numpy(), sxh.numpy(),
-                         rh.numpy(), ih.numpy())
-
-    step_host()
-    e2e_steps = max(3, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        step_host()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    pkg.linmin_destroy(h_host)
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = e2e = None
+    if not args.no_e2e:
+        e2e_s = run_e2e(pkg, cube, max(3, args.steps // 2))
+        if ws > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": N * ws / e2e_s, "unit": "pixels/s",
+               "h2d_bytes_per_step": N * L * 4 + L * 4,
+               "d2h_bytes_per_step": N * (2 * P + 2) * 4}
     if rank != 0:
         dist.barrier() if ws > 1 else None
         return
@@ -280,9 +298,7 @@ def main():
                      "mean_iters": float(iters.mean().item())},
         "phase_ms": {k: v / args.steps for k, v in phase_tot.items()},
         "not_converged": nbad,
-        "e2e": {"value": N * ws / e2e_s, "unit": "pixels/s",
-                "h2d_bytes_per_step": N * L * 4 + L * 4,
-                "d2h_bytes_per_step": N * (2 * P + 2) * 4},
+        "e2e": e2e,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,

@@ -48,6 +48,9 @@ constexpr int IPM_WARPS = 4;
 // registers at once).
 #define LM_STEP_FENCE() asm volatile("" ::: "memory")
 constexpr int IPM_THREADS = IPM_WARPS * 32;
+#ifndef IPM_MIN_BLOCKS
+#define IPM_MIN_BLOCKS 3
+#endif
 
 struct IpmArgs {
     long long N;
@@ -72,10 +75,11 @@ struct IpmCfg {
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
     static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
     static constexpr __host__ __device__ int collen(int k) { return PP - alignrow(k); }
+    // sum_{q<k} collen(q) = k*PP - 4*sum_{m=1..k} floor(m/4), in closed form
+    // (cheap when k is a runtime row index)
     static constexpr __host__ __device__ int colstart(int k) {
-        int s = 0;
-        for (int q = 0; q < k; ++q) s += collen(q);
-        return s;
+        const int A = k / 4;
+        return k * PP - 4 * (2 * A * (A - 1) + A * (k - 4 * A + 1));
     }
     static constexpr int LBUF = colstart(PP);
     // per-group floats: L columns + x broadcast; stride = 4 (mod 32) words
@@ -89,7 +93,7 @@ struct IpmCfg {
 };
 
 template <int NS, int G, bool ACC>
-__global__ void __launch_bounds__(IPM_THREADS)
+__global__ void __launch_bounds__(IPM_THREADS, IPM_MIN_BLOCKS)
 ipm_kernel(const IpmArgs a)
 {
     using C = IpmCfg<NS, G>;
@@ -237,38 +241,41 @@ ipm_kernel(const IpmArgs a)
         dec = group_max(dmx, G);
     };
 
-    while (__any_sync(FULL, alive)) {
+    // All warps of a block iterate together (one block barrier per trip):
+    // they then fetch the same instructions at about the same time, which
+    // keeps the large unrolled loop body in the instruction cache.
+    while (__syncthreads_or(alive)) {
         residual();
 
-        // ---- leave the active set / refill (per group)
+        // ---- leave the active set / refill (per group); a warp in which a
+        // group refilled starts the trip again so that the new pixel gets its
+        // residual before its first Newton step
         bool done;
         if (!ACC) done = (mu <= a.mu_ref) || (it >= a.max_iter);
         else done = ((rdmax <= a.tol_d) && (dec <= a.tol_c)) || (it >= a.max_iter);
         done = done && alive;
-        if (__any_sync(FULL, done)) {
-            if (done) {
-                const size_t base = (size_t)pix * P;
+        if (done) {
+            const size_t base = (size_t)pix * P;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    const int i = s * G + t;
-                    if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
-                }
-                const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
-                if (t == 0) {
-                    a.nu_state[pix] = nu;
-                    if (!ACC) a.it_state[pix] = it;
-                    else {
-                        a.it_state[pix] = conv ? it : -it;
-                        if (!conv) atomicAdd(a.n_notconv, 1ULL);
-                    }
-                }
-                pix = fetch();
-                alive = pix < a.N;
-                if (alive) load_pixel(pix);
+            for (int s = 0; s < NS; ++s) {
+                const int i = s * G + t;
+                if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
             }
-            residual();
+            const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
+            if (t == 0) {
+                a.nu_state[pix] = nu;
+                if (!ACC) a.it_state[pix] = it;
+                else {
+                    a.it_state[pix] = conv ? it : -it;
+                    if (!conv) atomicAdd(a.n_notconv, 1ULL);
+                }
+            }
+            pix = fetch();
+            alive = pix < a.N;
+            if (alive) load_pixel(pix);
         }
-        if (!__any_sync(FULL, alive)) break;
+        if (__any_sync(FULL, done)) continue;
+        if (!__any_sync(FULL, alive)) continue;
 
         // ---- barrier Hessian H = G~ + diag(lambda / x), lower rows in registers
         float H[NS][PP];
@@ -297,7 +304,7 @@ ipm_kernel(const IpmArgs a)
         }
 
         // ---- factorise H = L L^T; eliminate rhs B1 = 1, B2 = r_aff = -r_d - lambda
-        float B1[NS], B2[NS];
+        float B1[NS], B2[NS], dinv[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             B1[s] = valid[s] ? 1.f : 0.f;
@@ -319,7 +326,7 @@ ipm_kernel(const IpmArgs a)
             }
             float z1 = 0.f, z2 = 0.f;
             if (t == tk) {
-                H[sk][k] = r;                 // keep 1 / L_kk on the diagonal
+                dinv[sk] = r;                 // 1 / L_kk, kept by the row's owner
                 z1 = B1[sk] * r; z2 = B2[sk] * r;
                 B1[sk] = z1; B2[sk] = z2;
             }
@@ -365,17 +372,20 @@ ipm_kernel(const IpmArgs a)
             // scheduler prefetches one step ahead instead of hoisting the
             // loads of every step (which spills registers)
             int dep = 0;
+            int cb[NS];     // column i = s*G + t starts at cb[s] + alignrow(i)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int i = s * G + t;
+                cb[s] = C::colstart(i) - C::alignrow(i);
+            }
 #pragma unroll
             for (int k = PP - 1; k >= 0; --k) {
                 const int sk = k / G, tk = k % G;
                 float lk[NS];
 #pragma unroll
-                for (int s = 0; s <= sk; ++s) {
-                    const int i = s * G + t;
-                    lk[s] = colbuf[C::colstart(i) - C::alignrow(i) + k + dep];
-                }
+                for (int s = 0; s <= sk; ++s) lk[s] = colbuf[cb[s] + k + dep];
                 float w = 0.f;
-                if (t == tk) { w = v[sk] * H[sk][k]; v[sk] = w; }
+                if (t == tk) { w = v[sk] * dinv[sk]; v[sk] = w; }
                 w = __shfl_sync(FULL, w, tk, G);
                 dep = (w == w) ? 0 : 1;
 #pragma unroll
@@ -385,20 +395,25 @@ ipm_kernel(const IpmArgs a)
                 }
             }
         };
-        // forward solve L z = b in place with the register rows of L
+        // forward solve L z = b in place, L read from the stored columns
         auto fwd_solve = [&](float (&b)[NS]) {
+            int dep = 0;
 #pragma unroll
             for (int k = 0; k < PP; ++k) {
                 const int sk = k / G, tk = k % G;
+                float lk[NS];
+#pragma unroll
+                for (int s = sk; s < NS; ++s)
+                    lk[s] = colbuf[C::colstart(k) + s * G + t - C::alignrow(k) + dep];
                 float z = 0.f;
-                if (t == tk) { z = b[sk] * H[sk][k]; b[sk] = z; }
+                if (t == tk) { z = b[sk] * dinv[sk]; b[sk] = z; }
                 z = __shfl_sync(FULL, z, tk, G);
+                dep = (z == z) ? 0 : 1;
 #pragma unroll
                 for (int s = sk; s < NS; ++s) {
                     const bool below = (s > sk) || (t > tk);
-                    if (below) b[s] = fmaf(-H[s][k], z, b[s]);
+                    if (below) b[s] = fmaf(-lk[s], z, b[s]);
                 }
-                LM_STEP_FENCE();
             }
         };
 
