@@ -169,6 +169,49 @@ LINMIN_API const char *linmin_last_error(linmin_handle h);
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);
 
+/* Size in MiB of the static device scratch array of linmin_unmix_noalloc. */
+#define LINMIN_NOALLOC_SCRATCH_MB 64
+
+/*
+ * linmin_unmix_noalloc — the same unmixing as linmin_unmix for callers that
+ * cannot allocate device memory: code running where cudaMalloc is not
+ * allowed or not wanted, such as inside a host callback, a plugin that
+ * must not touch its host application's memory pool, or a process that
+ * has already reserved all device memory for itself.  It allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine, no handle): its
+ * scratch lives in one file-scope __device__ array of
+ * LINMIN_NOALLOC_SCRATCH_MB MiB, which every GPU that loads this library
+ * holds until the process exits.  The paper has no counterpart: this is
+ * an integration entry point, not part of the method.
+ *
+ *   library, cube, sigma, outputs: as in linmin_create/linmin_unmix, but
+ *            every non-NULL pointer must be device memory (else
+ *            LINMIN_ERR_INVALID);
+ *   cuda_stream: the cudaStream_t to run on (NULL: default stream); the
+ *            call queues its work and returns without synchronising.
+ * Limit: the scratch needed is, with every piece rounded up to 256 bytes,
+ *   2 P^2 doubles + 1 double + 2 PP^2 + PP + P + 2 L*PQ floats + 1 int
+ *   + 4 uint64 + N (4 P + 2) 4-byte words  <=  LINMIN_NOALLOC_SCRATCH_MB MiB
+ *   (PP = P rounded up to the kernel bucket 8, 16, 32, 40 or 48; PQ = P
+ *   rounded up to a multiple of 4); for L = 184, P = 36 that is about
+ *   114,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
+ * Unlike linmin_create it does not check rank [S^T; 1^T] = P: the caller
+ *   guarantees a library whose constrained minimiser is unique.
+ * Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture on that device.
+ * Concurrency: every call on a device shares the one array, and a call
+ *   leaves its contents behind (counters are cleared at the start of each
+ *   call).  Calls whose work overlaps on the GPU (different streams, or
+ *   different host threads) race on it: serialise them on one stream.
+ * Non-converged pixels are reported by iterations < 0 only.
+ */
+LINMIN_API linmin_status linmin_unmix_noalloc(const float *library, int L, int P,
+                                              const float *cube, long long N,
+                                              const float *sigma, float *abundances,
+                                              float *uncertainties, float *residual_rms,
+                                              int *iterations, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,172 @@
+// linmin_unmix_noalloc: the unmixing path with every scratch buffer carved
+// out of one statically sized device array, for callers that cannot
+// allocate device memory (see include/linmin.h).
+//
+// The array is a file-scope __device__ object: each GPU that loads this
+// library reserves it for the life of the process.  Host code cannot use
+// the symbol as a device address; the address is looked up once per device
+// with cudaGetSymbolAddress (first call on that device) and cached.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ipm.cuh"
+#include "kernels.cuh"
+#include "linmin.h"
+
+using namespace lm;
+
+namespace {
+
+constexpr size_t NOALLOC_BYTES = (size_t)LINMIN_NOALLOC_SCRATCH_MB << 20;
+constexpr int MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_mu;
+void *g_addr[MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (looked up on
+// the first call per device, with that device current).
+cudaError_t scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return cudaSuccess;
+}
+
+// Bump allocator over the scratch array (256-byte aligned pieces).
+struct Carve {
+    unsigned char *base;
+    size_t off = 0, cap;
+    template <typename T>
+    T *take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += (n ? n : 1) * sizeof(T);
+        return p;
+    }
+};
+
+size_t scratch_needed(int L, int P, int PP, long long N)
+{
+    Carve c{nullptr, 0, 0};
+    const int PQ = pq_of(P);
+    c.take<double>((size_t)P * P);
+    c.take<double>((size_t)P * P);
+    c.take<double>(1);
+    c.take<float>((size_t)PP * PP);
+    c.take<float>((size_t)PP * PP);
+    c.take<float>(PP);
+    c.take<float>(P);
+    c.take<float>((size_t)L * PQ);
+    c.take<float>((size_t)L * PQ);
+    c.take<int>(1);
+    c.take<unsigned long long>(4);
+    for (int k = 0; k < 4; ++k) c.take<float>((size_t)N * P);
+    c.take<float>(N);
+    c.take<int>(N);
+    return c.off;
+}
+
+bool is_device(const void *p)
+{
+    if (!p) return true;   // NULL outputs are allowed
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const float *cube,
+                                   long long N, const float *sigma, float *abundances,
+                                   float *uncertainties, float *residual_rms, int *iterations,
+                                   void *cuda_stream)
+{
+    if (N < 0 || !library || (N > 0 && (!cube || !sigma))) return LINMIN_ERR_INVALID;
+    Bucket b;
+    if (P < 1 || P > LINMIN_MAX_P || !ipm_bucket(P, &b)) return LINMIN_ERR_UNSUPPORTED;
+    if (L < P || L > LINMIN_MAX_L) return LINMIN_ERR_INVALID;
+    if (N == 0) return LINMIN_OK;
+    // beyond the static array: refuse (limit stated with LINMIN_NOALLOC_SCRATCH_MB)
+    if (scratch_needed(L, P, b.PP, N) > NOALLOC_BYTES) return LINMIN_ERR_INVALID;
+    if (!is_device(library) || !is_device(cube) || !is_device(sigma) || !is_device(abundances) ||
+        !is_device(uncertainties) || !is_device(residual_rms) || !is_device(iterations))
+        return LINMIN_ERR_INVALID;
+    void *base = nullptr;
+    cudaError_t e = scratch_address(&base);
+    if (e != cudaSuccess) return LINMIN_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int PP = b.PP, PQ = pq_of(P);
+    Carve c{(unsigned char *)base, 0, NOALLOC_BYTES};
+    Prep pr;
+    pr.G64 = c.take<double>((size_t)P * P);
+    pr.Gt64 = c.take<double>((size_t)P * P);
+    pr.scale = c.take<double>(1);
+    pr.Ghi = c.take<float>((size_t)PP * PP);
+    pr.Glo = c.take<float>((size_t)PP * PP);
+    pr.grs = c.take<float>(PP);
+    pr.gdiag = c.take<float>(P);
+    pr.Bhi = c.take<float>((size_t)L * PQ);
+    pr.Blo = c.take<float>((size_t)L * PQ);
+    pr.flags = c.take<int>(1);
+    unsigned long long *cnt = c.take<unsigned long long>(4);
+    float *c_hi = c.take<float>((size_t)N * P);
+    float *c_lo = c.take<float>((size_t)N * P);
+    float *xs = c.take<float>((size_t)N * P);
+    float *lam = c.take<float>((size_t)N * P);
+    float *nu = c.take<float>(N);
+    int *its = c.take<int>(N);
+
+#define NA_CUDA(call)                                  \
+    do {                                               \
+        if ((call) != cudaSuccess) return LINMIN_ERR_CUDA; \
+    } while (0)
+    // the array keeps the previous call's contents: zero the counters/flags
+    NA_CUDA(cudaMemsetAsync(pr.flags, 0, sizeof(int), st));
+    NA_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), st));
+    NA_CUDA(launch_prep(library, sigma, L, P, PP, pr, st));
+    NA_CUDA(launch_project(cube, N, L, P, pr.Bhi, pr.Blo, c_hi, c_lo, st));
+    linmin_options o;
+    linmin_default_options(&o);
+    IpmArgs ia;
+    ia.N = N; ia.P = P; ia.max_iter = o.max_iter;
+    ia.c_hi = c_hi; ia.c_lo = c_lo;
+    ia.Ghi = pr.Ghi; ia.Glo = pr.Glo; ia.grs = pr.grs;
+    ia.x_state = xs; ia.lam_state = lam; ia.nu_state = nu; ia.it_state = its;
+    ia.n_notconv = cnt + 2;
+    ia.mu_ref = o.refine_mu; ia.tol_c = o.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    ia.counter = cnt + 0;
+    NA_CUDA(launch_ipm(b, false, ia, st));
+    ia.counter = cnt + 1;
+    NA_CUDA(launch_ipm(b, true, ia, st));
+    float *x_out = abundances ? abundances : xs;
+    RefineArgs ra;
+    ra.N = N; ra.P = P; ra.Gt64 = pr.Gt64; ra.scale = pr.scale; ra.gdiag = pr.gdiag;
+    ra.c_hi = c_hi; ra.c_lo = c_lo; ra.x_in = xs; ra.lam_in = lam;
+    ra.x_out = x_out; ra.sx_out = uncertainties; ra.n_unverified = cnt + 3;
+    ra.tol_x = 1e-9; ra.tol_g = 1e-9;
+    NA_CUDA(launch_refine(ra, st));
+    if (residual_rms) NA_CUDA(launch_rms(cube, library, x_out, N, L, P, residual_rms, st));
+    if (iterations)
+        NA_CUDA(cudaMemcpyAsync(iterations, its, (size_t)N * sizeof(int),
+                                cudaMemcpyDeviceToDevice, st));
+#undef NA_CUDA
+    return LINMIN_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_
                 5: "ERR_TIMEOUT", 6: "ERR_NOT_CONVERGED", 7: "ERR_UNSUPPORTED"}
 
 EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_wait",
-            "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version")
+            "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version",
+            "linmin_unmix_noalloc")
+LINMIN_NOALLOC_SCRATCH_MB = 64
 PHASES = ("prep", "project", "ipm_f32", "ipm_df", "refine", "rms")
 
 
@@ -76,6 +78,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_destroy.restype = ctypes.c_int
     lib.linmin_last_error.argtypes = [H]
     lib.linmin_last_error.restype = ctypes.c_char_p
+    lib.linmin_unmix_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_longlong,
+                                         P, P, P, P, P, ctypes.c_void_p]
+    lib.linmin_unmix_noalloc.restype = ctypes.c_int
     lib.linmin_version.argtypes = []
     lib.linmin_version.restype = ctypes.c_char_p
     return lib
@@ -161,6 +166,16 @@ def linmin_destroy(h) -> int:
 def linmin_last_error(h=None) -> str:
     s = lib().linmin_last_error(h)
     return s.decode() if s else ""
+
+
+def linmin_unmix_noalloc(library, L: int, P: int, cube, N: int, sigma, abundances=None,
+                         uncertainties=None, residual_rms=None, iterations=None,
+                         stream=None) -> int:
+    """The allocation-free variant (device pointers only); returns the status."""
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    return lib().linmin_unmix_noalloc(_ptr(library), int(L), int(P), _ptr(cube), int(N),
+                                      _ptr(sigma), _ptr(abundances), _ptr(uncertainties),
+                                      _ptr(residual_rms), _ptr(iterations, "int32"), st)
 
 
 def linmin_version() -> str:
