@@ -310,6 +310,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
 
     RefineArgs ra;
     ra.N = N; ra.P = P; ra.Gt64 = h->prep.Gt64; ra.scale = h->prep.scale; ra.gdiag = h->prep.gdiag;
+    ra.Ghi = h->prep.Ghi; ra.Glo = h->prep.Glo; ra.PP = h->bucket.PP;
     ra.c_hi = h->c_hi; ra.c_lo = h->c_lo; ra.x_in = h->x; ra.lam_in = h->lam;
     ra.x_out = d_x; ra.sx_out = d_sx; ra.n_unverified = h->dcnt + 3;
     ra.tol_x = 1e-9; ra.tol_g = 1e-9;

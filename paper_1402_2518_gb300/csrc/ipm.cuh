@@ -48,9 +48,6 @@ constexpr int IPM_WARPS = 4;
 // registers at once).
 #define LM_STEP_FENCE() asm volatile("" ::: "memory")
 constexpr int IPM_THREADS = IPM_WARPS * 32;
-#ifndef IPM_MIN_BLOCKS
-#define IPM_MIN_BLOCKS 3
-#endif
 
 struct IpmArgs {
     long long N;
@@ -72,6 +69,9 @@ struct IpmCfg {
     static constexpr int NS = NS_, G = G_;
     static constexpr int PP = NS * G;      // padded size, multiple of 4
     static constexpr int GPW = 32 / G;     // pixel groups per warp
+    // resident blocks per SM the register budget is sized for: 9 slots of
+    // 4 lanes hold 180 registers of H per lane, so 2 blocks; others 3
+    static constexpr int MIN_BLOCKS = NS >= 8 ? 2 : 3;
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
     static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
     static constexpr __host__ __device__ int collen(int k) { return PP - alignrow(k); }
@@ -93,7 +93,7 @@ struct IpmCfg {
 };
 
 template <int NS, int G, bool ACC>
-__global__ void __launch_bounds__(IPM_THREADS, IPM_MIN_BLOCKS)
+__global__ void __launch_bounds__(IPM_THREADS, IpmCfg<NS, G>::MIN_BLOCKS)
 ipm_kernel(const IpmArgs a)
 {
     using C = IpmCfg<NS, G>;
@@ -189,24 +189,32 @@ ipm_kernel(const IpmArgs a)
 #pragma unroll
         for (int s = 0; s < NS; ++s) xbuf[s * G + t] = x[s];
         __syncwarp();
+        if (!ACC) {
+            float acc[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int i = s * G + t;
-            const float *grow = sGhi + i * PP;
-            float gx;
-            if (!ACC) {
-                float acc = 0.f;
+            for (int s = 0; s < NS; ++s) acc[s] = 0.f;
 #pragma unroll
-                for (int j4 = 0; j4 < PP / 4; ++j4) {
-                    const float4 g = *reinterpret_cast<const float4 *>(grow + 4 * j4);
-                    const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
-                    acc = fmaf(g.x, xv.x, acc);
-                    acc = fmaf(g.y, xv.y, acc);
-                    acc = fmaf(g.z, xv.z, acc);
-                    acc = fmaf(g.w, xv.w, acc);
+            for (int j4 = 0; j4 < PP / 4; ++j4) {
+                const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) {
+                    const float4 g = *reinterpret_cast<const float4 *>(sGhi + (s * G + t) * PP + 4 * j4);
+                    acc[s] = fmaf(g.x, xv.x, acc[s]);
+                    acc[s] = fmaf(g.y, xv.y, acc[s]);
+                    acc[s] = fmaf(g.z, xv.z, acc[s]);
+                    acc[s] = fmaf(g.w, xv.w, acc[s]);
                 }
-                gx = acc - (valid[s] ? __ldg(a.c_hi + cbase + i) : 0.f);
-            } else {
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float gx = acc[s] - (valid[s] ? __ldg(a.c_hi + cbase + s * G + t) : 0.f);
+                rd[s] = valid[s] ? (gx - lam[s]) + nu : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int i = s * G + t;
+                const float *grow = sGhi + i * PP;
                 const float *glow = sGlo + i * PP;
                 dot2 d;
 #pragma unroll
@@ -221,10 +229,10 @@ ipm_kernel(const IpmArgs a)
                 }
                 if (valid[s]) d.add_df(df{-__ldg(a.c_hi + cbase + i), -__ldg(a.c_lo + cbase + i)});
                 const df r = d.result();
-                gx = r.hi + r.lo;
+                const float gx = r.hi + r.lo;
+                rd[s] = valid[s] ? (gx - lam[s]) + nu : 0.f;
+                LM_STEP_FENCE();
             }
-            rd[s] = valid[s] ? (gx - lam[s]) + nu : 0.f;
-            LM_STEP_FENCE();
         }
         __syncwarp();
         float sx = 0.f, sxl = 0.f, rmax = 0.f, dmx = 0.f;
@@ -279,7 +287,7 @@ ipm_kernel(const IpmArgs a)
 
         // ---- barrier Hessian H = G~ + diag(lambda / x), lower rows in registers
         float H[NS][PP];
-        auto Dof = [&](int s) -> float { return valid[s] ? fminf(lam[s] / x[s], DMAX) : 1.f; };
+        auto Dof = [&](int s) -> float { return valid[s] ? fminf(__fdividef(lam[s], x[s]), DMAX) : 1.f; };
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const int i = s * G + t;
@@ -432,8 +440,8 @@ ipm_kernel(const IpmArgs a)
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             dla[s] = valid[s] ? fmaf(-Dof(s), dxa[s], -lam[s]) : 0.f;
-            if (valid[s] && dxa[s] < 0.f) ap = fminf(ap, -x[s] / dxa[s]);
-            if (valid[s] && dla[s] < 0.f) ad = fminf(ad, -lam[s] / dla[s]);
+            if (valid[s] && dxa[s] < 0.f) ap = fminf(ap, __fdividef(-x[s], dxa[s]));
+            if (valid[s] && dla[s] < 0.f) ad = fminf(ad, __fdividef(-lam[s], dla[s]));
         }
         ap = group_min(ap, G);
         ad = group_min(ad, G);
@@ -449,7 +457,7 @@ ipm_kernel(const IpmArgs a)
         float corr[NS], zc[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            corr[s] = valid[s] ? fmaf(dxa[s], dla[s], -smu) / x[s] : 0.f;
+            corr[s] = valid[s] ? __fdividef(fmaf(dxa[s], dla[s], -smu), x[s]) : 0.f;
             zc[s] = -corr[s];
         }
         fwd_solve(zc);
@@ -467,8 +475,8 @@ ipm_kernel(const IpmArgs a)
         for (int s = 0; s < NS; ++s) {
             dx[s] = dxa[s] + zc[s];
             dl[s] = valid[s] ? fmaf(-Dof(s), dx[s], -lam[s] - corr[s]) : 0.f;
-            if (valid[s] && dx[s] < 0.f) ap = fminf(ap, -x[s] / dx[s]);
-            if (valid[s] && dl[s] < 0.f) ad = fminf(ad, -lam[s] / dl[s]);
+            if (valid[s] && dx[s] < 0.f) ap = fminf(ap, __fdividef(-x[s], dx[s]));
+            if (valid[s] && dl[s] < 0.f) ad = fminf(ad, __fdividef(-lam[s], dl[s]));
         }
         ap = group_min(ap, G);
         ad = group_min(ad, G);

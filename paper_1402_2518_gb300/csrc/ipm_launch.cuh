@@ -35,6 +35,7 @@ cudaError_t launch_ipm_mode(const IpmArgs &a, cudaStream_t st)
 LM_DECLARE_BUCKET(2, 4)
 LM_DECLARE_BUCKET(4, 4)
 LM_DECLARE_BUCKET(4, 8)
+LM_DECLARE_BUCKET(9, 4)
 LM_DECLARE_BUCKET(5, 8)
 LM_DECLARE_BUCKET(3, 16)
 

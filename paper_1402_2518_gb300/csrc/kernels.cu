@@ -224,17 +224,18 @@ refine_kernel(const RefineArgs a)
     for (int r = 0; r < k; ++r)
         for (int c = 0; c <= r; ++c) mat(r, c) = sG[idx[r] * P + idx[c]];
     // Cholesky of G~_SS (positive definite when rank [S^T; 1^T] = P)
+    // the diagonal of M keeps 1 / L_cc (one division per column)
     bool ok = true;
     for (int c = 0; c < k; ++c) {
         double d = mat(c, c);
         for (int m = 0; m < c; ++m) d -= mat(c, m) * mat(c, m);
         if (!(d > 0.0)) { ok = false; d = 1e-300; }
-        const double lc = sqrt(d);
-        mat(c, c) = lc;
+        const double rl = 1.0 / sqrt(d);
+        mat(c, c) = rl;
         for (int r = c + 1; r < k; ++r) {
             double sacc = mat(r, c);
             for (int m = 0; m < c; ++m) sacc -= mat(r, m) * mat(c, m);
-            mat(r, c) = sacc / lc;
+            mat(r, c) = sacc * rl;
         }
     }
     // forward: u = L^-1 1, v = L^-1 c~_S
@@ -242,8 +243,8 @@ refine_kernel(const RefineArgs a)
         double su = 1.0;
         double sv = (double)a.c_hi[base + idx[r]] + (double)a.c_lo[base + idx[r]];
         for (int m = 0; m < r; ++m) { su -= mat(r, m) * u[m]; sv -= mat(r, m) * v[m]; }
-        u[r] = su / mat(r, r);
-        v[r] = sv / mat(r, r);
+        u[r] = su * mat(r, r);
+        v[r] = sv * mat(r, r);
     }
     double a11 = 0.0, a1b = 0.0;
     for (int r = 0; r < k; ++r) { a11 += u[r] * u[r]; a1b += u[r] * v[r]; }
@@ -252,19 +253,36 @@ refine_kernel(const RefineArgs a)
     for (int r = k - 1; r >= 0; --r) {
         double sx = v[r] - nu * u[r], su = u[r];
         for (int m = r + 1; m < k; ++m) { sx -= mat(m, r) * xs[m]; su -= mat(m, r) * u[m]; }
-        xs[r] = sx / mat(r, r);
-        u[r] = su / mat(r, r);
+        xs[r] = sx * mat(r, r);
+        u[r] = su * mat(r, r);
     }
-    // KKT check off the support: lambda_i = (G~ x)_i - c~_i + nu >= -tol
+    // KKT check off the support: lambda_i = (G~ x)_i - c~_i + nu >= -tol,
+    // evaluated in double-float (G~ and x_S as float32 hi + lo pairs) on the
+    // float32 pipes; fp64 runs at a small fraction of the float32 rate here
     double xmin = 1.0, lmin = 0.0, xsum = 0.0;
-    for (int r = 0; r < k; ++r) { xmin = fmin(xmin, xs[r]); xsum += fmax(xs[r], 0.0); }
+    float xh[KMAX], xl[KMAX];
+    for (int r = 0; r < k; ++r) {
+        xmin = fmin(xmin, xs[r]);
+        xsum += fmax(xs[r], 0.0);
+        const df d = split_double(xs[r]);
+        xh[r] = d.hi; xl[r] = d.lo;
+    }
     {
+        const df nud = split_double(nu);
         int r = 0;
         for (int i = 0; i < P; ++i) {
             if (r < k && idx[r] == i) { ++r; continue; }
-            double g = -((double)a.c_hi[base + i] + (double)a.c_lo[base + i]) + nu;
-            for (int q = 0; q < k; ++q) g += sG[i * P + idx[q]] * xs[q];
-            lmin = fmin(lmin, g);
+            dot2 g;
+            const float *ghi = a.Ghi + (size_t)i * a.PP, *glo = a.Glo + (size_t)i * a.PP;
+            for (int q = 0; q < k; ++q) {
+                const float gh = __ldg(ghi + idx[q]), gl = __ldg(glo + idx[q]);
+                g.add_prod(gh, xh[q]);
+                g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+            }
+            g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
+            g.add_df(nud);
+            const df gv = g.result();
+            lmin = fmin(lmin, (double)gv.hi + (double)gv.lo);
         }
     }
     const bool verified = ok && xmin >= -a.tol_x && lmin >= -a.tol_g && xsum > 0.0;
@@ -293,7 +311,7 @@ refine_kernel(const RefineArgs a)
                 for (int m = r; m < k; ++m) {
                     double sacc = (m == r) ? 1.0 : 0.0;
                     for (int q = r; q < m; ++q) sacc -= mat(m, q) * w[q];
-                    w[m] = sacc / mat(m, m);
+                    w[m] = sacc * mat(m, m);
                     dinv += w[m] * w[m];
                 }
                 const double var = dinv - u[r] * u[r] / a11;

@@ -38,6 +38,8 @@ struct RefineArgs {
     long long N;
     int P;
     const double *Gt64;            // P x P
+    const float *Ghi, *Glo;        // PP x PP, G~ as hi + lo float32
+    int PP;
     const double *scale;
     const float *gdiag;            // P
     const float *c_hi, *c_lo;      // N x P

@@ -157,6 +157,7 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     float *x_out = abundances ? abundances : xs;
     RefineArgs ra;
     ra.N = N; ra.P = P; ra.Gt64 = pr.Gt64; ra.scale = pr.scale; ra.gdiag = pr.gdiag;
+    ra.Ghi = pr.Ghi; ra.Glo = pr.Glo; ra.PP = PP;
     ra.c_hi = c_hi; ra.c_lo = c_lo; ra.x_in = xs; ra.lam_in = lam;
     ra.x_out = x_out; ra.sx_out = uncertainties; ra.n_unverified = cnt + 3;
     ra.tol_x = 1e-9; ra.tol_g = 1e-9;
