@@ -36,6 +36,23 @@ METRIC = "pixels/s IPLS unmix at <=1e-4 abs err vs FP64 oracle; served p50/p99 l
 FP32_LANES_PER_SM = 128
 KERNELS_PER_STEP = 8   # prep x3, projection, IPM x2, refinement, rms
 
+# DRAM bytes per pixel of the two interior-point launches, from the ncu
+# capture summarised in profiles/ipm_refine_project_rms_omega65k_full.md
+# (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels).  Valid
+# only for the kernel source it was measured on (hash of csrc/ipm.cuh).
+IPM_TRAFFIC = {"ipm_sha256_12": "e5215b5b06b3",
+               "bytes_per_pixel": (9.756928e6 + 0.497408e6 + 38.651392e6 + 0.470016e6) / 65536}
+
+
+def ipm_traffic(n_pix: int):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1402_2518_gb300", "csrc", "ipm.cuh")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:12]
+    if h != IPM_TRAFFIC["ipm_sha256_12"]:
+        return None
+    return IPM_TRAFFIC["bytes_per_pixel"] * n_pix
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -292,7 +309,10 @@ def main():
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"kernel": "ipm (float32 + double-float residual phases)",
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": ipm_traffic(N),
+                     "traffic_note": "DRAM bytes per call of both IPM launches (ncu, scaled "
+                                     "from 65,536 pixels by pixel count)",
                      "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "flops_per_iter": flop_per_iter,
                      "mean_iters": float(iters.mean().item())},
