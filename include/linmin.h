@@ -36,8 +36,9 @@
  *                   criterion has no 1/2, its Hessian is 2G);
  *     residual_rms  N, sqrt(mean_l (y_l - sum_j x_j S_jl)^2), unwhitened;
  *     iterations    int32 N, interior-point iterations used; negative when
- *                   the pixel did not reach the stopping test within
- *                   max_iter (its last iterate is returned).
+ *                   the pixel needed the retry path and did not reach its
+ *                   stopping test within max_iter (its last iterate is
+ *                   returned).
  *   Any output pointer may be NULL; that output is then not written.
  * - Pointers may be host or device memory (detected per call).  With device
  *   pointers the call is stream-ordered on the handle's stream and does not
@@ -91,11 +92,11 @@ typedef struct {
     int precision;        /* LINMIN_PROJ_DF */
     int constraint;       /* LINMIN_STO */
     int max_iter;         /* interior-point iteration cap per pixel (default 100) */
-    float tol;            /* complementarity tolerance: each coordinate ends with
-                             min(x_i, lambda_i / s) <= tol, s = trace(G)/P
-                             (default 1e-9) */
-    float refine_mu;      /* switch to the double-float KKT residual once
-                             mu / s <= refine_mu (default 1e-9) */
+    float tol;            /* retry path: complementarity tolerance, each
+                             coordinate ends with min(x_i, lambda_i / s) <= tol,
+                             s = trace(G)/P (default 1e-9) */
+    float refine_mu;      /* retry path: switch to the double-float KKT
+                             residual once mu / s <= refine_mu (default 1e-9) */
     void *cuda_stream;    /* cudaStream_t the handle runs on; NULL = default */
     int profile;          /* non-zero: record CUDA events around each phase of
                              linmin_unmix (see linmin_phase_times); default 0 */
@@ -105,9 +106,11 @@ typedef struct {
 enum {
     LINMIN_PHASE_PREP = 0,      /* whitening, fp64 Gram, splits (3 kernels) */
     LINMIN_PHASE_PROJECT = 1,   /* double-float projection c = S W^2 y */
-    LINMIN_PHASE_IPM_F32 = 2,   /* interior point, float32 residual */
-    LINMIN_PHASE_IPM_DF = 3,    /* interior point, double-float residual */
-    LINMIN_PHASE_REFINE = 4,    /* fp64 support solve + uncertainties */
+    LINMIN_PHASE_IPM = 2,       /* interior point, float32 residual, all pixels */
+    LINMIN_PHASE_CROSSOVER = 3, /* fp64 active-set finish + uncertainties */
+    LINMIN_PHASE_RETRY = 4,     /* pixels the crossover could not finish:
+                                   interior point with the double-float
+                                   residual, then the crossover again */
     LINMIN_PHASE_RMS = 5,       /* residual RMS */
     LINMIN_NUM_PHASES = 6
 };
@@ -132,9 +135,11 @@ LINMIN_API linmin_status linmin_create(const float *library, int L, int P,
 
 /*
  * Unmix N pixels: whitening (Sec. 2.3), projection c = S W^2 y,
- * primal-dual interior-point FCLS per pixel (Sec. 2.2), extended precision
- * KKT refinement on the support, abundance uncertainties (Sec. 2.3) and
- * the RMS of the fit.
+ * primal-dual interior-point FCLS per pixel (Sec. 2.2) until the support of
+ * the solution is identified, an fp64 active-set crossover to the exact
+ * minimiser (the few pixels it cannot finish are re-solved with a
+ * double-float KKT residual), abundance uncertainties (Sec. 2.3) and the RMS
+ * of the fit.
  *   cube  N x L float32, host or device;  N >= 0 (N = 0 is a no-op);
  *   sigma L float32 > 0, host or device;
  *   outputs as in the conventions (NULL = skip).
@@ -191,10 +196,10 @@ LINMIN_API const char *linmin_version(void);
  *            call queues its work and returns without synchronising.
  * Limit: the scratch needed is, with every piece rounded up to 256 bytes,
  *   2 P^2 doubles + 1 double + 2 PP^2 + PP + P + 2 L*PQ floats + 1 int
- *   + 4 uint64 + N (4 P + 2) 4-byte words  <=  LINMIN_NOALLOC_SCRATCH_MB MiB
+ *   + 8 uint64 + N (4 P + 4) 4-byte words  <=  LINMIN_NOALLOC_SCRATCH_MB MiB
  *   (PP = P rounded up to the kernel bucket 8, 16, 32, 40 or 48; PQ = P
  *   rounded up to a multiple of 4); for L = 184, P = 36 that is about
- *   114,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
+ *   113,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
  * Unlike linmin_create it does not check rank [S^T; 1^T] = P: the caller
  *   guarantees a library whose constrained minimiser is unique.
  * Set-up: the first call on a device looks up the array's device address

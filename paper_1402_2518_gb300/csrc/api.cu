@@ -3,9 +3,13 @@
 // A call of linmin_unmix queues, on the handle's stream:
 //   1. library preparation for this sigma (fp64 Gram, scale, hi/lo splits);
 //   2. the double-float projection c~ = B~^T y + rho;
-//   3. the interior-point kernel, float32 residual phase, until mu <= mu_ref;
-//   4. the interior-point kernel, double-float residual phase, to the stop test;
-//   5. the fp64 support refinement (abundances, uncertainties);
+//   3. the interior-point kernel with the float32 residual, every pixel,
+//      until mu <= mu_stop (the support is then identified);
+//   4. the fp64 active-set crossover to the exact minimiser (abundances,
+//      uncertainties); pixels it cannot finish go to a retry list;
+//   5. retry list only: interior point from the start, float32 residual to
+//      mu <= refine_mu then double-float residual to the stop test, and the
+//      crossover again;
 //   6. the RMS of the fit.
 // Host pointers are staged through handle-owned device buffers.
 #include <cuda_runtime.h>
@@ -32,12 +36,15 @@ struct linmin_ctx {
 
     float *dS = nullptr;               // P x L library
     Prep prep{};                       // per-sigma buffers
-    unsigned long long *dcnt = nullptr;// [0] phase-A counter, [1] phase-B counter,
-                                       // [2] not converged, [3] unverified refinements
+    unsigned long long *dcnt = nullptr;// [0] IPM work counter, [1] retry IPM (float32),
+                                       // [2] not converged, [3] unverified after retry,
+                                       // [4] retry IPM (double-float), [5] retry list length,
+                                       // [6] crossover failures of the first pass
     // per-pixel scratch
     long long capN = 0;
     float *c_hi = nullptr, *c_lo = nullptr, *x = nullptr, *lam = nullptr, *nu = nullptr;
     int *it = nullptr;
+    long long *retry = nullptr;
     // host-pointer staging
     long long capIO = 0;
     float *io_cube = nullptr, *io_sigma = nullptr, *io_x = nullptr, *io_sx = nullptr,
@@ -189,7 +196,7 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     A(dalloc(&h->prep.Bhi, (size_t)L * PQ));
     A(dalloc(&h->prep.Blo, (size_t)L * PQ));
     A(dalloc(&h->prep.flags, 1));
-    A(dalloc(&h->dcnt, 4));
+    A(dalloc(&h->dcnt, 8));
     A(cudaMemcpy(h->dS, hS.data(), hS.size() * 4, cudaMemcpyHostToDevice));
     if (o.profile)
         for (int i = 0; i <= LINMIN_NUM_PHASES; ++i) A(cudaEventCreate(&h->ev[i]));
@@ -215,6 +222,7 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     A(dalloc(&h->lam, np));
     A(dalloc(&h->nu, (size_t)N));
     A(dalloc(&h->it, (size_t)N));
+    A(dalloc(&h->retry, (size_t)N));
 #undef A
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
@@ -286,7 +294,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     int *d_it = iterations ? (dev_out[3] ? iterations : h->io_it) : nullptr;
 
     LM_CUDA(h, cudaMemsetAsync(h->prep.flags, 0, sizeof(int), st), "memset");
-    LM_CUDA(h, cudaMemsetAsync(h->dcnt, 0, 4 * sizeof(unsigned long long), st), "memset");
+    LM_CUDA(h, cudaMemsetAsync(h->dcnt, 0, 8 * sizeof(unsigned long long), st), "memset");
     mark(h, 0);
     LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
     mark(h, 1);
@@ -300,21 +308,33 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
     ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
     ia.n_notconv = h->dcnt + 2;
-    ia.mu_ref = h->opt.refine_mu; ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
-    ia.counter = h->dcnt + 0;
-    LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel (float32 residual)");
+    ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    ia.list = nullptr; ia.list_len = nullptr;
+    // 3. all pixels: float32 residual until mu <= mu_stop
+    ia.mu_ref = MU_STOP; ia.counter = h->dcnt + 0;
+    LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel");
     mark(h, 3);
-    ia.counter = h->dcnt + 1;
-    LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "interior-point kernel (double-float residual)");
-    mark(h, 4);
-
+    // 4. crossover; failures appended to the retry list
     RefineArgs ra;
     ra.N = N; ra.P = P; ra.Gt64 = h->prep.Gt64; ra.scale = h->prep.scale; ra.gdiag = h->prep.gdiag;
     ra.Ghi = h->prep.Ghi; ra.Glo = h->prep.Glo; ra.PP = h->bucket.PP;
     ra.c_hi = h->c_hi; ra.c_lo = h->c_lo; ra.x_in = h->x; ra.lam_in = h->lam;
-    ra.x_out = d_x; ra.sx_out = d_sx; ra.n_unverified = h->dcnt + 3;
-    ra.tol_x = 1e-9; ra.tol_g = 1e-9;
-    LM_CUDA(h, launch_refine(ra, st), "refinement kernel");
+    ra.x_out = d_x; ra.sx_out = d_sx; ra.n_unverified = h->dcnt + 6;
+    ra.tol_x = 1e-9; ra.tol_g = 1e-9; ra.max_swaps = MAX_SWAPS;
+    ra.list = nullptr; ra.list_len = nullptr;
+    ra.retry_list = h->retry; ra.retry_len = h->dcnt + 5;
+    LM_CUDA(h, launch_refine(ra, st), "crossover kernel");
+    mark(h, 4);
+    // 5. retry list: the interior point from the start with the accurate
+    //    residual phase, then the crossover again
+    ia.list = h->retry; ia.list_len = h->dcnt + 5;
+    ia.mu_ref = h->opt.refine_mu; ia.counter = h->dcnt + 1;
+    LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "retry interior-point kernel (float32)");
+    ia.counter = h->dcnt + 4;
+    LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "retry interior-point kernel (double-float)");
+    ra.list = h->retry; ra.list_len = h->dcnt + 5;
+    ra.retry_list = nullptr; ra.retry_len = nullptr; ra.n_unverified = h->dcnt + 3;
+    LM_CUDA(h, launch_refine(ra, st), "retry crossover kernel");
     mark(h, 5);
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);

@@ -61,6 +61,8 @@ struct IpmArgs {
     int *it_state;                 // N: iterations so far (phase A) / final (phase B, <0: cap)
     unsigned long long *counter;   // pixel work counter, zeroed before the launch
     unsigned long long *n_notconv; // phase B: number of pixels that hit max_iter
+    const long long *list;         // optional: pixels to process (else 0..N-1)
+    const unsigned long long *list_len;  // number of entries of list
     float mu_ref, tol_c, tol_d, eta;
 };
 
@@ -130,11 +132,16 @@ ipm_kernel(const IpmArgs a)
     int it = 0;
     size_t cbase = 0;   // offset of the current pixel in the N x P arrays
 
+    // pixel work list: 0..N-1, or the first list_len entries of list
+    const unsigned long long n_work = a.list ? *a.list_len : (unsigned long long)a.N;
     auto fetch = [&]() -> long long {
         unsigned long long v = 0;
-        if (t == 0) v = atomicAdd(a.counter, 1ULL);
-        v = __shfl_sync(gmask, v, 0, G);
-        return (long long)v;
+        long long p = a.N;                      // a.N marks "no more work"
+        if (t == 0) {
+            v = atomicAdd(a.counter, 1ULL);
+            if (v < n_work) p = a.list ? a.list[v] : (long long)v;
+        }
+        return __shfl_sync(gmask, p, 0, G);
     };
 
     // load c~ and either the start point (phase A) or the saved state (B)

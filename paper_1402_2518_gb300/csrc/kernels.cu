@@ -7,12 +7,12 @@
 //            (Dot2) so that c~ keeps ~48 bits: the FCLS minimiser moves by
 //            up to 1e-2 when c~ is merely rounded to float32 on these
 //            libraries (constrained condition numbers up to ~1e6).
-//   refine   one fp64 KKT solve on the support S of the interior-point
-//            solution: x_S from [[G~_SS, 1],[1^T, 0]] [x_S; nu] = [c~_S; 1],
-//            checked against the KKT conditions off S; the abundance
-//            uncertainty (Sec. 2.3, "error from the Hessian") is the square
-//            root of the diagonal of the top-left block of the inverse of
-//            that bordered matrix, divided by s.
+//   refine   fp64 active-set crossover from the interior-point iterate:
+//            x_S from [[G~_SS, 1],[1^T, 0]] [x_S; nu] = [c~_S; 1] on a
+//            support S, with swaps until the KKT conditions hold; the
+//            abundance uncertainty (Sec. 2.3, "error from the Hessian") is
+//            the square root of the diagonal of the top-left block of the
+//            inverse of that bordered matrix, divided by s.
 //   rms      sqrt(mean_l (y_l - sum_j x_j S_jl)^2), unwhitened.
 #include "common.cuh"
 #include "ipm.cuh"
@@ -195,9 +195,19 @@ cudaError_t launch_project(const float *cube, long long N, int L, int P, const f
     }
 }
 
-// ------------------------------------------------------ fp64 refinement
+// ------------------------------------------------ fp64 crossover/refinement
 constexpr int REF_THREADS = 128;
 
+// Exact finish of the interior-point solution by an active-set crossover:
+// start from the support S the iterate suggests (lambda_i < x_i G_ii), solve
+// the equality-constrained problem on S in fp64 (bordered KKT system through
+// the Cholesky factor of G~_SS, positive definite since rank [S^T; 1^T] = P),
+// then drop the most negative coordinate, or add the coordinate whose
+// multiplier lambda_i = (G~ x)_i - c~_i + nu is the most negative, and
+// re-solve, until x_S >= -tol_x and lambda >= -tol_g off S (the KKT
+// conditions of Sec. 2.2's problem) or max_swaps is reached.  On success x
+// is the minimiser to fp64 accuracy and the uncertainty is read off the same
+// factor; otherwise the pixel is appended to the retry list.
 template <int KMAX>
 __global__ void __launch_bounds__(REF_THREADS)
 refine_kernel(const RefineArgs a)
@@ -206,8 +216,10 @@ refine_kernel(const RefineArgs a)
     const int P = a.P;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) sG[e] = a.Gt64[e];
     __syncthreads();
-    const long long n = (long long)blockIdx.x * REF_THREADS + threadIdx.x;
-    if (n >= a.N) return;
+    const long long slot = (long long)blockIdx.x * REF_THREADS + threadIdx.x;
+    const unsigned long long n_work = a.list ? *a.list_len : (unsigned long long)a.N;
+    if (slot >= (long long)n_work) return;
+    const long long n = a.list ? a.list[slot] : slot;
     const size_t base = (size_t)n * P;
 
     int idx[KMAX];
@@ -221,74 +233,108 @@ refine_kernel(const RefineArgs a)
     }
     if (k == 0) idx[k++] = imax;
     auto mat = [&](int r, int c) -> double & { return M[r * (r + 1) / 2 + c]; };
-    for (int r = 0; r < k; ++r)
-        for (int c = 0; c <= r; ++c) mat(r, c) = sG[idx[r] * P + idx[c]];
-    // Cholesky of G~_SS (positive definite when rank [S^T; 1^T] = P)
-    // the diagonal of M keeps 1 / L_cc (one division per column)
-    bool ok = true;
-    for (int c = 0; c < k; ++c) {
-        double d = mat(c, c);
-        for (int m = 0; m < c; ++m) d -= mat(c, m) * mat(c, m);
-        if (!(d > 0.0)) { ok = false; d = 1e-300; }
-        const double rl = 1.0 / sqrt(d);
-        mat(c, c) = rl;
-        for (int r = c + 1; r < k; ++r) {
-            double sacc = mat(r, c);
-            for (int m = 0; m < c; ++m) sacc -= mat(r, m) * mat(c, m);
-            mat(r, c) = sacc * rl;
-        }
-    }
-    // forward: u = L^-1 1, v = L^-1 c~_S
-    for (int r = 0; r < k; ++r) {
-        double su = 1.0;
-        double sv = (double)a.c_hi[base + idx[r]] + (double)a.c_lo[base + idx[r]];
-        for (int m = 0; m < r; ++m) { su -= mat(r, m) * u[m]; sv -= mat(r, m) * v[m]; }
-        u[r] = su * mat(r, r);
-        v[r] = sv * mat(r, r);
-    }
-    double a11 = 0.0, a1b = 0.0;
-    for (int r = 0; r < k; ++r) { a11 += u[r] * u[r]; a1b += u[r] * v[r]; }
-    const double nu = (a1b - 1.0) / a11;
-    // back: xs = L^-T (v - nu u), u <- L^-T u (= G~_SS^-1 1)
-    for (int r = k - 1; r >= 0; --r) {
-        double sx = v[r] - nu * u[r], su = u[r];
-        for (int m = r + 1; m < k; ++m) { sx -= mat(m, r) * xs[m]; su -= mat(m, r) * u[m]; }
-        xs[r] = sx * mat(r, r);
-        u[r] = su * mat(r, r);
-    }
-    // KKT check off the support: lambda_i = (G~ x)_i - c~_i + nu >= -tol,
-    // evaluated in double-float (G~ and x_S as float32 hi + lo pairs) on the
-    // float32 pipes; fp64 runs at a small fraction of the float32 rate here
-    double xmin = 1.0, lmin = 0.0, xsum = 0.0;
-    float xh[KMAX], xl[KMAX];
-    for (int r = 0; r < k; ++r) {
-        xmin = fmin(xmin, xs[r]);
-        xsum += fmax(xs[r], 0.0);
-        const df d = split_double(xs[r]);
-        xh[r] = d.hi; xl[r] = d.lo;
-    }
-    {
-        const df nud = split_double(nu);
-        int r = 0;
-        for (int i = 0; i < P; ++i) {
-            if (r < k && idx[r] == i) { ++r; continue; }
-            dot2 g;
-            const float *ghi = a.Ghi + (size_t)i * a.PP, *glo = a.Glo + (size_t)i * a.PP;
-            for (int q = 0; q < k; ++q) {
-                const float gh = __ldg(ghi + idx[q]), gl = __ldg(glo + idx[q]);
-                g.add_prod(gh, xh[q]);
-                g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+
+    bool ok = false, fact_ok = true;
+    double nu = 0.0, a11 = 1.0, xsum = 1.0;
+    for (int sw = 0; sw <= a.max_swaps; ++sw) {
+        // Cholesky of G~_SS; the diagonal keeps 1 / L_cc
+        for (int r = 0; r < k; ++r)
+            for (int c = 0; c <= r; ++c) mat(r, c) = sG[idx[r] * P + idx[c]];
+        fact_ok = true;
+        for (int c = 0; c < k; ++c) {
+            double d = mat(c, c);
+            for (int m = 0; m < c; ++m) d -= mat(c, m) * mat(c, m);
+            if (!(d > 0.0)) { fact_ok = false; d = 1e-300; }
+            const double rl = 1.0 / sqrt(d);
+            mat(c, c) = rl;
+            for (int r = c + 1; r < k; ++r) {
+                double sacc = mat(r, c);
+                for (int m = 0; m < c; ++m) sacc -= mat(r, m) * mat(c, m);
+                mat(r, c) = sacc * rl;
             }
-            g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
-            g.add_df(nud);
-            const df gv = g.result();
-            lmin = fmin(lmin, (double)gv.hi + (double)gv.lo);
         }
+        // forward: u = L^-1 1, v = L^-1 c~_S
+        for (int r = 0; r < k; ++r) {
+            double su = 1.0;
+            double sv = (double)a.c_hi[base + idx[r]] + (double)a.c_lo[base + idx[r]];
+            for (int m = 0; m < r; ++m) { su -= mat(r, m) * u[m]; sv -= mat(r, m) * v[m]; }
+            u[r] = su * mat(r, r);
+            v[r] = sv * mat(r, r);
+        }
+        a11 = 0.0;
+        double a1b = 0.0;
+        for (int r = 0; r < k; ++r) { a11 += u[r] * u[r]; a1b += u[r] * v[r]; }
+        nu = (a1b - 1.0) / a11;
+        // back: xs = L^-T (v - nu u), u <- L^-T u (= G~_SS^-1 1)
+        for (int r = k - 1; r >= 0; --r) {
+            double sx = v[r] - nu * u[r], su = u[r];
+            for (int m = r + 1; m < k; ++m) { sx -= mat(m, r) * xs[m]; su -= mat(m, r) * u[m]; }
+            xs[r] = sx * mat(r, r);
+            u[r] = su * mat(r, r);
+        }
+        if (!fact_ok) break;
+        // most negative coordinate on S
+        int rneg = -1;
+        double xmin = -a.tol_x;
+        xsum = 0.0;
+        for (int r = 0; r < k; ++r) {
+            if (xs[r] < xmin) { xmin = xs[r]; rneg = r; }
+            xsum += fmax(xs[r], 0.0);
+        }
+        if (rneg >= 0) {
+            if (sw == a.max_swaps || k == 1) break;
+            for (int r = rneg; r + 1 < k; ++r) idx[r] = idx[r + 1];
+            --k;
+            continue;
+        }
+        // most negative multiplier off S, in double-float (G~ and x_S as
+        // float32 hi + lo pairs) on the float32 pipes
+        float xh[KMAX], xl[KMAX];
+        for (int r = 0; r < k; ++r) {
+            const df d = split_double(xs[r]);
+            xh[r] = d.hi; xl[r] = d.lo;
+        }
+        const df nud = split_double(nu);
+        int iadd = -1;
+        double lmin = -a.tol_g;
+        {
+            int r = 0;
+            for (int i = 0; i < P; ++i) {
+                if (r < k && idx[r] == i) { ++r; continue; }
+                dot2 g;
+                const float *ghi = a.Ghi + (size_t)i * a.PP, *glo = a.Glo + (size_t)i * a.PP;
+                for (int q = 0; q < k; ++q) {
+                    const float gh = __ldg(ghi + idx[q]), gl = __ldg(glo + idx[q]);
+                    g.add_prod(gh, xh[q]);
+                    g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+                }
+                g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
+                g.add_df(nud);
+                const df gv = g.result();
+                const double lam_i = (double)gv.hi + (double)gv.lo;
+                if (lam_i < lmin) { lmin = lam_i; iadd = i; }
+            }
+        }
+        if (iadd >= 0) {
+            if (sw == a.max_swaps || k >= KMAX) break;
+            int r = k;
+            while (r > 0 && idx[r - 1] > iadd) { idx[r] = idx[r - 1]; --r; }
+            idx[r] = iadd;
+            ++k;
+            continue;
+        }
+        ok = xsum > 0.0;
+        break;
     }
-    const bool verified = ok && xmin >= -a.tol_x && lmin >= -a.tol_g && xsum > 0.0;
-    if (!verified && a.n_unverified) atomicAdd(a.n_unverified, 1ULL);
-    // abundances
-    if (verified) {
+    if (!ok) {
+        if (a.retry_list) {
+            const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
+            a.retry_list[pos] = n;
+        }
+        if (a.n_unverified) atomicAdd(a.n_unverified, 1ULL);
+    }
+    // abundances: the crossover solution, or the interior-point iterate
+    if (ok) {
         int r = 0;
         for (int i = 0; i < P; ++i) {
             float xi = 0.f;
@@ -298,7 +344,7 @@ refine_kernel(const RefineArgs a)
     } else if (a.x_out != a.x_in) {
         for (int i = 0; i < P; ++i) a.x_out[base + i] = a.x_in[base + i];
     }
-    // uncertainties: [K^-1]_rr = (G~_SS^-1)_rr - u_r^2 / (1^T G~_SS^-1 1)
+    // uncertainties on the final support: [K^-1]_rr = (G~_SS^-1)_rr - u_r^2 / (1^T G~_SS^-1 1)
     if (a.sx_out) {
         const double s = a.scale[0];
         double w[KMAX];
@@ -330,7 +376,7 @@ static cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(refine_kernel<KMAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (a.N + REF_THREADS - 1) / REF_THREADS;
+    const long long blocks = (a.N + REF_THREADS - 1) / REF_THREADS;   // list mode: <= N entries
     refine_kernel<KMAX><<<(unsigned)blocks, REF_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }

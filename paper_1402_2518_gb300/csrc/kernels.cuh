@@ -6,6 +6,12 @@
 namespace lm {
 
 constexpr double RHO = 1.0;   // rho of G~ = G / s + rho 1 1^T (see ipm.cuh)
+// The first interior-point pass stops once mu / s <= MU_STOP: the support is
+// then identified on almost every pixel and the crossover finishes it with
+// at most MAX_SWAPS support changes (measured on the synthetic workloads:
+// ~0.5 changes per pixel on average, at most a few).
+constexpr float MU_STOP = 1e-11f;
+constexpr int MAX_SWAPS = 8;
 
 // Bucket of the interior-point kernel for a library size P.
 struct Bucket { int NS, G, PP; };
@@ -46,8 +52,13 @@ struct RefineArgs {
     const float *x_in, *lam_in;    // N x P (interior-point result)
     float *x_out;                  // N x P (may alias x_in)
     float *sx_out;                 // N x P or NULL
-    unsigned long long *n_unverified;   // pixels whose support solve failed the KKT check
+    unsigned long long *n_unverified;   // pixels whose crossover did not reach KKT
     double tol_x, tol_g;
+    int max_swaps;                 // support changes allowed before giving up
+    const long long *list;         // optional: pixels to process (else 0..N-1)
+    const unsigned long long *list_len;
+    long long *retry_list;         // optional: pixels that failed, appended
+    unsigned long long *retry_len;
 };
 cudaError_t launch_refine(const RefineArgs &a, cudaStream_t st);
 

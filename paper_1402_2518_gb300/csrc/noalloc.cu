@@ -73,10 +73,11 @@ size_t scratch_needed(int L, int P, int PP, long long N)
     c.take<float>((size_t)L * PQ);
     c.take<float>((size_t)L * PQ);
     c.take<int>(1);
-    c.take<unsigned long long>(4);
+    c.take<unsigned long long>(8);
     for (int k = 0; k < 4; ++k) c.take<float>((size_t)N * P);
     c.take<float>(N);
     c.take<int>(N);
+    c.take<long long>(N);
     return c.off;
 }
 
@@ -124,13 +125,14 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     pr.Bhi = c.take<float>((size_t)L * PQ);
     pr.Blo = c.take<float>((size_t)L * PQ);
     pr.flags = c.take<int>(1);
-    unsigned long long *cnt = c.take<unsigned long long>(4);
+    unsigned long long *cnt = c.take<unsigned long long>(8);
     float *c_hi = c.take<float>((size_t)N * P);
     float *c_lo = c.take<float>((size_t)N * P);
     float *xs = c.take<float>((size_t)N * P);
     float *lam = c.take<float>((size_t)N * P);
     float *nu = c.take<float>(N);
     int *its = c.take<int>(N);
+    long long *retry = c.take<long long>(N);
 
 #define NA_CUDA(call)                                  \
     do {                                               \
@@ -138,7 +140,7 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     } while (0)
     // the array keeps the previous call's contents: zero the counters/flags
     NA_CUDA(cudaMemsetAsync(pr.flags, 0, sizeof(int), st));
-    NA_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), st));
+    NA_CUDA(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), st));
     NA_CUDA(launch_prep(library, sigma, L, P, PP, pr, st));
     NA_CUDA(launch_project(cube, N, L, P, pr.Bhi, pr.Blo, c_hi, c_lo, st));
     linmin_options o;
@@ -149,18 +151,26 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     ia.Ghi = pr.Ghi; ia.Glo = pr.Glo; ia.grs = pr.grs;
     ia.x_state = xs; ia.lam_state = lam; ia.nu_state = nu; ia.it_state = its;
     ia.n_notconv = cnt + 2;
-    ia.mu_ref = o.refine_mu; ia.tol_c = o.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
-    ia.counter = cnt + 0;
+    ia.tol_c = o.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    ia.list = nullptr; ia.list_len = nullptr;
+    ia.mu_ref = MU_STOP; ia.counter = cnt + 0;
     NA_CUDA(launch_ipm(b, false, ia, st));
-    ia.counter = cnt + 1;
-    NA_CUDA(launch_ipm(b, true, ia, st));
     float *x_out = abundances ? abundances : xs;
     RefineArgs ra;
     ra.N = N; ra.P = P; ra.Gt64 = pr.Gt64; ra.scale = pr.scale; ra.gdiag = pr.gdiag;
     ra.Ghi = pr.Ghi; ra.Glo = pr.Glo; ra.PP = PP;
     ra.c_hi = c_hi; ra.c_lo = c_lo; ra.x_in = xs; ra.lam_in = lam;
-    ra.x_out = x_out; ra.sx_out = uncertainties; ra.n_unverified = cnt + 3;
-    ra.tol_x = 1e-9; ra.tol_g = 1e-9;
+    ra.x_out = x_out; ra.sx_out = uncertainties; ra.n_unverified = cnt + 6;
+    ra.tol_x = 1e-9; ra.tol_g = 1e-9; ra.max_swaps = MAX_SWAPS;
+    ra.list = nullptr; ra.list_len = nullptr; ra.retry_list = retry; ra.retry_len = cnt + 5;
+    NA_CUDA(launch_refine(ra, st));
+    ia.list = retry; ia.list_len = cnt + 5;
+    ia.mu_ref = o.refine_mu; ia.counter = cnt + 1;
+    NA_CUDA(launch_ipm(b, false, ia, st));
+    ia.counter = cnt + 4;
+    NA_CUDA(launch_ipm(b, true, ia, st));
+    ra.list = retry; ra.list_len = cnt + 5;
+    ra.retry_list = nullptr; ra.retry_len = nullptr; ra.n_unverified = cnt + 3;
     NA_CUDA(launch_refine(ra, st));
     if (residual_rms) NA_CUDA(launch_rms(cube, library, x_out, N, L, P, residual_rms, st));
     if (iterations)

@@ -33,7 +33,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version",
             "linmin_unmix_noalloc")
 LINMIN_NOALLOC_SCRATCH_MB = 64
-PHASES = ("prep", "project", "ipm_f32", "ipm_df", "refine", "rms")
+PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
 
 
 class linmin_options(ctypes.Structure):

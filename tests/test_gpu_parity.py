@@ -185,10 +185,19 @@ def test_sigma_scaling_invariance(pkg):
 
 
 def test_not_converged_reported(pkg):
-    cube = synth.make_cube(synth.OMEGA_262K, n_pix=200)
-    gpu = run_gpu(pkg, cube.S, cube.sigma, cube.X, max_iter=3)
-    assert gpu["status"] == 6 and gpu["n_notconv"] == 200
-    assert np.all(gpu["iters"] < 0)
+    """With a 1-iteration cap the crossover still finishes many pixels
+    exactly; the rest hit the cap on the retry path.  Negative iteration
+    counts, the reported count and the status agree, and every pixel that
+    is reported converged is correct."""
+    cube = synth.make_cube(synth.OMEGA_262K, n_pix=300)
+    gpu = run_gpu(pkg, cube.S, cube.sigma, cube.X, max_iter=1)
+    bad = gpu["iters"] < 0
+    assert gpu["n_notconv"] == int(bad.sum())
+    assert gpu["status"] == (6 if bad.any() else 0)
+    assert bad.any(), "a 1-iteration cap should leave some pixels unfinished"
+    ref = oracle.unmix(cube.S, cube.sigma, cube.X)
+    good = ~bad
+    assert np.abs(gpu["x"][good] - ref["x"][good]).max() <= X_TOL
 
 
 def test_invalid_sigma_and_empty(pkg):
