@@ -196,10 +196,11 @@ LINMIN_API const char *linmin_version(void);
  *            call queues its work and returns without synchronising.
  * Limit: the scratch needed is, with every piece rounded up to 256 bytes,
  *   2 P^2 doubles + 1 double + 2 PP^2 + PP + P + 2 L*PQ floats + 1 int
- *   + 8 uint64 + N (4 P + 4) 4-byte words  <=  LINMIN_NOALLOC_SCRATCH_MB MiB
+ *   + 20 + P uint64 + P + 1 uint32 + N (4 P + 11) 4-byte words
+ *   <=  LINMIN_NOALLOC_SCRATCH_MB MiB
  *   (PP = P rounded up to the kernel bucket 8, 16, 32, 40 or 48; PQ = P
  *   rounded up to a multiple of 4); for L = 184, P = 36 that is about
- *   113,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
+ *   107,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
  * Unlike linmin_create it does not check rank [S^T; 1^T] = P: the caller
  *   guarantees a library whose constrained minimiser is unique.
  * Set-up: the first call on a device looks up the array's device address

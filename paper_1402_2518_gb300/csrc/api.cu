@@ -45,6 +45,8 @@ struct linmin_ctx {
     float *c_hi = nullptr, *c_lo = nullptr, *x = nullptr, *lam = nullptr, *nu = nullptr;
     int *it = nullptr;
     long long *retry = nullptr;
+    unsigned long long *mask = nullptr;
+    CrossoverScratch xw{};
     // host-pointer staging
     long long capIO = 0;
     float *io_cube = nullptr, *io_sigma = nullptr, *io_x = nullptr, *io_sx = nullptr,
@@ -197,6 +199,10 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     A(dalloc(&h->prep.Blo, (size_t)L * PQ));
     A(dalloc(&h->prep.flags, 1));
     A(dalloc(&h->dcnt, 8));
+    A(dalloc(&h->xw.len, (size_t)MAX_SWAPS + 2));
+    A(dalloc(&h->xw.len_all, 1));
+    A(dalloc(&h->xw.cursor, (size_t)P + 1));
+    A(dalloc(&h->xw.hist, (size_t)P + 1));
     A(cudaMemcpy(h->dS, hS.data(), hS.size() * 4, cudaMemcpyHostToDevice));
     if (o.profile)
         for (int i = 0; i <= LINMIN_NUM_PHASES; ++i) A(cudaEventCreate(&h->ev[i]));
@@ -223,6 +229,10 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     A(dalloc(&h->nu, (size_t)N));
     A(dalloc(&h->it, (size_t)N));
     A(dalloc(&h->retry, (size_t)N));
+    A(dalloc(&h->mask, (size_t)N));
+    A(dalloc(&h->xw.list[0], (size_t)N));
+    A(dalloc(&h->xw.list[1], (size_t)N));
+    A(dalloc(&h->xw.ksize, (size_t)N));
 #undef A
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
@@ -315,15 +325,14 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel");
     mark(h, 3);
     // 4. crossover; failures appended to the retry list
-    RefineArgs ra;
-    ra.N = N; ra.P = P; ra.Gt64 = h->prep.Gt64; ra.scale = h->prep.scale; ra.gdiag = h->prep.gdiag;
-    ra.Ghi = h->prep.Ghi; ra.Glo = h->prep.Glo; ra.PP = h->bucket.PP;
-    ra.c_hi = h->c_hi; ra.c_lo = h->c_lo; ra.x_in = h->x; ra.lam_in = h->lam;
-    ra.x_out = d_x; ra.sx_out = d_sx; ra.n_unverified = h->dcnt + 6;
-    ra.tol_x = 1e-9; ra.tol_g = 1e-9; ra.max_swaps = MAX_SWAPS;
-    ra.list = nullptr; ra.list_len = nullptr;
-    ra.retry_list = h->retry; ra.retry_len = h->dcnt + 5;
-    LM_CUDA(h, launch_refine(ra, st), "crossover kernel");
+    CrossArgs ca{};
+    ca.N = N; ca.P = P; ca.Gt64 = h->prep.Gt64; ca.Ghi = h->prep.Ghi; ca.Glo = h->prep.Glo;
+    ca.PP = h->bucket.PP; ca.scale = h->prep.scale; ca.gdiag = h->prep.gdiag;
+    ca.c_hi = h->c_hi; ca.c_lo = h->c_lo; ca.x_in = h->x; ca.lam_in = h->lam;
+    ca.x_out = d_x; ca.sx_out = d_sx; ca.mask = h->mask;
+    ca.retry_list = h->retry; ca.retry_len = h->dcnt + 5; ca.n_unverified = nullptr;
+    ca.tol_x = 1e-9; ca.tol_g = 1e-9;
+    LM_CUDA(h, launch_crossover(ca, h->xw, nullptr, nullptr, st), "crossover kernels");
     mark(h, 4);
     // 5. retry list: the interior point from the start with the accurate
     //    residual phase, then the crossover again
@@ -332,9 +341,8 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "retry interior-point kernel (float32)");
     ia.counter = h->dcnt + 4;
     LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "retry interior-point kernel (double-float)");
-    ra.list = h->retry; ra.list_len = h->dcnt + 5;
-    ra.retry_list = nullptr; ra.retry_len = nullptr; ra.n_unverified = h->dcnt + 3;
-    LM_CUDA(h, launch_refine(ra, st), "retry crossover kernel");
+    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = h->dcnt + 3;
+    LM_CUDA(h, launch_crossover(ca, h->xw, h->retry, h->dcnt + 5, st), "retry crossover kernels");
     mark(h, 5);
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
@@ -394,7 +402,9 @@ linmin_status linmin_destroy(linmin_handle h)
         if (e) cudaEventDestroy(e);
     void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
                     h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
-                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->io_cube, h->io_sigma,
+                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
+                    h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
+                    h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
                     h->io_x, h->io_sx, h->io_rms, h->io_it};
     for (void *p : ptrs)
         if (p) cudaFree(p);

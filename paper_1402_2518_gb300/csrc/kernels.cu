@@ -198,196 +198,279 @@ cudaError_t launch_project(const float *cube, long long N, int L, int P, const f
 // ------------------------------------------------ fp64 crossover/refinement
 constexpr int REF_THREADS = 128;
 
-// Exact finish of the interior-point solution by an active-set crossover:
-// start from the support S the iterate suggests (lambda_i < x_i G_ii), solve
-// the equality-constrained problem on S in fp64 (bordered KKT system through
-// the Cholesky factor of G~_SS, positive definite since rank [S^T; 1^T] = P),
-// then drop the most negative coordinate, or add the coordinate whose
-// multiplier lambda_i = (G~ x)_i - c~_i + nu is the most negative, and
-// re-solve, until x_S >= -tol_x and lambda >= -tol_g off S (the KKT
-// conditions of Sec. 2.2's problem) or max_swaps is reached.  On success x
-// is the minimiser to fp64 accuracy and the uncertainty is read off the same
-// factor; otherwise the pixel is appended to the retry list.
-template <int KMAX>
-__global__ void __launch_bounds__(REF_THREADS)
-refine_kernel(const RefineArgs a)
+// Support of the interior-point iterate as a bit mask per pixel: lambda_i <
+// theta x_i G_ii (theta = SUPPORT_THETA; coordinates whose barrier term is
+// far below their curvature), and the histogram of support sizes.
+__global__ void support_kernel(long long N, int P, const float *__restrict__ x,
+                               const float *__restrict__ lam, const float *__restrict__ gdiag,
+                               const long long *list, const unsigned long long *list_len,
+                               unsigned long long *__restrict__ mask, int *__restrict__ ksize,
+                               unsigned int *__restrict__ hist)
 {
-    extern __shared__ double sG[];
-    const int P = a.P;
-    for (int e = threadIdx.x; e < P * P; e += blockDim.x) sG[e] = a.Gt64[e];
-    __syncthreads();
-    const long long slot = (long long)blockIdx.x * REF_THREADS + threadIdx.x;
-    const unsigned long long n_work = a.list ? *a.list_len : (unsigned long long)a.N;
+    const long long slot = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned long long n_work = list ? *list_len : (unsigned long long)N;
     if (slot >= (long long)n_work) return;
-    const long long n = a.list ? a.list[slot] : slot;
+    const long long n = list ? list[slot] : slot;
     const size_t base = (size_t)n * P;
-
-    int idx[KMAX];
-    double M[KMAX * (KMAX + 1) / 2], u[KMAX], v[KMAX], xs[KMAX];
-    int k = 0, imax = 0;
+    unsigned long long m = 0;
+    int imax = 0;
     float best = -1.f;
     for (int i = 0; i < P; ++i) {
-        const float xi = a.x_in[base + i], li = a.lam_in[base + i];
+        const float xi = x[base + i], li = lam[base + i];
         if (xi > best) { best = xi; imax = i; }
-        if (li < xi * a.gdiag[i]) idx[k++] = i;
+        if (li < SUPPORT_THETA * xi * gdiag[i]) m |= 1ULL << i;
     }
-    if (k == 0) idx[k++] = imax;
-    auto mat = [&](int r, int c) -> double & { return M[r * (r + 1) / 2 + c]; };
+    if (!m) m = 1ULL << imax;
+    mask[n] = m;
+    const int kk = __popcll(m);
+    ksize[n] = kk;
+    if (hist) atomicAdd(hist + kk, 1u);
+}
 
-    bool ok = false, fact_ok = true;
-    double nu = 0.0, a11 = 1.0, xsum = 1.0;
-    for (int sw = 0; sw <= a.max_swaps; ++sw) {
-        // Cholesky of G~_SS; the diagonal keeps 1 / L_cc
-        for (int r = 0; r < k; ++r)
-            for (int c = 0; c <= r; ++c) mat(r, c) = sG[idx[r] * P + idx[c]];
-        fact_ok = true;
-        for (int c = 0; c < k; ++c) {
-            double d = mat(c, c);
-            for (int m = 0; m < c; ++m) d -= mat(c, m) * mat(c, m);
-            if (!(d > 0.0)) { fact_ok = false; d = 1e-300; }
-            const double rl = 1.0 / sqrt(d);
-            mat(c, c) = rl;
-            for (int r = c + 1; r < k; ++r) {
-                double sacc = mat(r, c);
-                for (int m = 0; m < c; ++m) sacc -= mat(r, m) * mat(c, m);
-                mat(r, c) = sacc * rl;
-            }
+// Exclusive prefix sum of the P+1 support-size counts (one block); *total
+// receives the number of listed pixels.
+__global__ void bucket_scan_kernel(int P, const unsigned int *__restrict__ hist,
+                                   unsigned long long *__restrict__ cursor,
+                                   unsigned long long *__restrict__ total)
+{
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int kk = 0; kk <= P; ++kk) { cursor[kk] = s; s += hist[kk]; }
+        *total = s;
+    }
+}
+
+// Pixels listed by increasing support size (counting sort), so that the
+// lanes of a warp run the O(k^3) crossover loops to similar k.
+__global__ void bucket_scatter_kernel(long long N, const int *__restrict__ ksize,
+                                      unsigned long long *__restrict__ cursor,
+                                      long long *__restrict__ list)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const unsigned long long pos = atomicAdd(cursor + ksize[n], 1ULL);
+    list[pos] = n;
+}
+
+// One pass of the active-set crossover.  For each listed pixel, solve the
+// equality-constrained problem on its support S (mask) in fp64 through the
+// Cholesky factor of G~_SS (positive definite since rank [S^T; 1^T] = P),
+// then check the KKT conditions of Sec. 2.2's problem: x_S >= -tol_x and
+// lambda_i = (G~ x)_i - c~_i + nu >= -tol_g off S.  If they hold, x is the
+// minimiser to fp64 accuracy: write it and its uncertainty (square root of
+// the diagonal of the top-left block of [[G~_SS, 1],[1^T, 0]]^-1, divided by
+// s).  Otherwise drop the most negative coordinate, or add the most
+// violated one, and hand the pixel to the next pass; on the last pass (or if
+// the factorisation fails) the pixel goes to the retry list.
+template <int KMAX>
+__global__ void __launch_bounds__(REF_THREADS)
+crossover_pass_kernel(const CrossArgs a)
+{
+    // G~ as hi + lo float32 words in shared memory (P x P)
+    extern __shared__ __align__(16) float sgm[];
+    const int P = a.P;
+    float *sGh = sgm, *sGl = sgm + P * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int i = e / P, j = e % P;
+        sGh[e] = a.Ghi[(size_t)i * a.PP + j];
+        sGl[e] = a.Glo[(size_t)i * a.PP + j];
+    }
+    __syncthreads();
+    const long long slot = (long long)blockIdx.x * REF_THREADS + threadIdx.x;
+    if (slot >= (long long)*a.len_in) return;
+    const long long n = a.list_in[slot];
+    const size_t base = (size_t)n * P;
+    const unsigned long long m = a.mask[n];
+
+    // all arithmetic below is double-float (two float32 words, ~48-bit
+    // significand) on the float32 pipes: fp64 is a small fraction of the
+    // fp32 rate on this GPU
+    int idx[KMAX];
+    df M[KMAX * (KMAX + 1) / 2], u[KMAX], v[KMAX], xs[KMAX];
+    int k = 0;
+    for (int i = 0; i < P; ++i)
+        if ((m >> i) & 1ULL) idx[k++] = i;
+    auto mat = [&](int r, int c) -> df & { return M[r * (r + 1) / 2 + c]; };
+    auto gt = [&](int i, int j) -> df { return df{sGh[i * P + j], sGl[i * P + j]}; };
+
+    // Cholesky of G~_SS; the diagonal keeps 1 / L_cc
+    for (int r = 0; r < k; ++r)
+        for (int c = 0; c <= r; ++c) mat(r, c) = gt(idx[r], idx[c]);
+    bool fact_ok = true;
+    for (int c = 0; c < k; ++c) {
+        df d = mat(c, c);
+        for (int q = 0; q < c; ++q) d = df_fms(d, mat(c, q), mat(c, q));
+        if (!(d.hi > 0.f)) { fact_ok = false; d = df_make(1e-30f); }
+        const df rl = df_rsqrt(d);
+        mat(c, c) = rl;
+        for (int r = c + 1; r < k; ++r) {
+            df sacc = mat(r, c);
+            for (int q = 0; q < c; ++q) sacc = df_fms(sacc, mat(r, q), mat(c, q));
+            mat(r, c) = df_mul(sacc, rl);
         }
-        // forward: u = L^-1 1, v = L^-1 c~_S
+    }
+    // forward: u = L^-1 1, v = L^-1 c~_S
+    for (int r = 0; r < k; ++r) {
+        df su = df_make(1.f);
+        df sv = df{a.c_hi[base + idx[r]], a.c_lo[base + idx[r]]};
+        for (int q = 0; q < r; ++q) { su = df_fms(su, mat(r, q), u[q]); sv = df_fms(sv, mat(r, q), v[q]); }
+        u[r] = df_mul(su, mat(r, r));
+        v[r] = df_mul(sv, mat(r, r));
+    }
+    df a11 = df_make(0.f), a1b = df_make(0.f);
+    for (int r = 0; r < k; ++r) { a11 = df_add(a11, df_mul(u[r], u[r])); a1b = df_add(a1b, df_mul(u[r], v[r])); }
+    const df nu = df_div(df_sub(a1b, df_make(1.f)), a11);
+    // back: xs = L^-T (v - nu u), u <- L^-T u (= G~_SS^-1 1)
+    for (int r = k - 1; r >= 0; --r) {
+        df sx = df_fms(v[r], nu, u[r]), su = u[r];
+        for (int q = r + 1; q < k; ++q) { sx = df_fms(sx, mat(q, r), xs[q]); su = df_fms(su, mat(q, r), u[q]); }
+        xs[r] = df_mul(sx, mat(r, r));
+        u[r] = df_mul(su, mat(r, r));
+    }
+    // decision
+    int flip = -1;             // coordinate whose membership in S changes
+    df xsum = df_make(0.f);
+    if (fact_ok) {
+        float xmin = (float)-a.tol_x;
         for (int r = 0; r < k; ++r) {
-            double su = 1.0;
-            double sv = (double)a.c_hi[base + idx[r]] + (double)a.c_lo[base + idx[r]];
-            for (int m = 0; m < r; ++m) { su -= mat(r, m) * u[m]; sv -= mat(r, m) * v[m]; }
-            u[r] = su * mat(r, r);
-            v[r] = sv * mat(r, r);
+            if (xs[r].hi < xmin) { xmin = xs[r].hi; flip = idx[r]; }
+            if (xs[r].hi > 0.f) xsum = df_add(xsum, xs[r]);
         }
-        a11 = 0.0;
-        double a1b = 0.0;
-        for (int r = 0; r < k; ++r) { a11 += u[r] * u[r]; a1b += u[r] * v[r]; }
-        nu = (a1b - 1.0) / a11;
-        // back: xs = L^-T (v - nu u), u <- L^-T u (= G~_SS^-1 1)
-        for (int r = k - 1; r >= 0; --r) {
-            double sx = v[r] - nu * u[r], su = u[r];
-            for (int m = r + 1; m < k; ++m) { sx -= mat(m, r) * xs[m]; su -= mat(m, r) * u[m]; }
-            xs[r] = sx * mat(r, r);
-            u[r] = su * mat(r, r);
-        }
-        if (!fact_ok) break;
-        // most negative coordinate on S
-        int rneg = -1;
-        double xmin = -a.tol_x;
-        xsum = 0.0;
-        for (int r = 0; r < k; ++r) {
-            if (xs[r] < xmin) { xmin = xs[r]; rneg = r; }
-            xsum += fmax(xs[r], 0.0);
-        }
-        if (rneg >= 0) {
-            if (sw == a.max_swaps || k == 1) break;
-            for (int r = rneg; r + 1 < k; ++r) idx[r] = idx[r + 1];
-            --k;
-            continue;
-        }
-        // most negative multiplier off S, in double-float (G~ and x_S as
-        // float32 hi + lo pairs) on the float32 pipes
-        float xh[KMAX], xl[KMAX];
-        for (int r = 0; r < k; ++r) {
-            const df d = split_double(xs[r]);
-            xh[r] = d.hi; xl[r] = d.lo;
-        }
-        const df nud = split_double(nu);
-        int iadd = -1;
-        double lmin = -a.tol_g;
-        {
-            int r = 0;
+        if (flip >= 0 && k == 1) flip = -2;       // cannot drop the last one
+        if (flip == -1) {
+            // most negative multiplier off S
+            float lmin = (float)-a.tol_g;
             for (int i = 0; i < P; ++i) {
-                if (r < k && idx[r] == i) { ++r; continue; }
+                if ((m >> i) & 1ULL) continue;
                 dot2 g;
-                const float *ghi = a.Ghi + (size_t)i * a.PP, *glo = a.Glo + (size_t)i * a.PP;
                 for (int q = 0; q < k; ++q) {
-                    const float gh = __ldg(ghi + idx[q]), gl = __ldg(glo + idx[q]);
-                    g.add_prod(gh, xh[q]);
-                    g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+                    const float gh = sGh[i * P + idx[q]], gl = sGl[i * P + idx[q]];
+                    g.add_prod(gh, xs[q].hi);
+                    g.c = fmaf(gh, xs[q].lo, fmaf(gl, xs[q].hi, g.c));
                 }
                 g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
-                g.add_df(nud);
+                g.add_df(nu);
                 const df gv = g.result();
-                const double lam_i = (double)gv.hi + (double)gv.lo;
-                if (lam_i < lmin) { lmin = lam_i; iadd = i; }
+                if (gv.hi < lmin) { lmin = gv.hi; flip = i; }
             }
         }
-        if (iadd >= 0) {
-            if (sw == a.max_swaps || k >= KMAX) break;
-            int r = k;
-            while (r > 0 && idx[r - 1] > iadd) { idx[r] = idx[r - 1]; --r; }
-            idx[r] = iadd;
-            ++k;
-            continue;
-        }
-        ok = xsum > 0.0;
-        break;
+    } else {
+        flip = -2;
     }
-    if (!ok) {
-        if (a.retry_list) {
-            const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
-            a.retry_list[pos] = n;
-        }
-        if (a.n_unverified) atomicAdd(a.n_unverified, 1ULL);
-    }
-    // abundances: the crossover solution, or the interior-point iterate
-    if (ok) {
+    if (flip == -1 && xsum.hi > 0.f) {
+        // KKT holds: abundances and uncertainties
         int r = 0;
         for (int i = 0; i < P; ++i) {
             float xi = 0.f;
-            if (r < k && idx[r] == i) { xi = (float)(fmax(xs[r], 0.0) / xsum); ++r; }
+            if ((m >> i) & 1ULL) { xi = xs[r].hi > 0.f ? df_div(xs[r], xsum).hi : 0.f; ++r; }
             a.x_out[base + i] = xi;
         }
-    } else if (a.x_out != a.x_in) {
-        for (int i = 0; i < P; ++i) a.x_out[base + i] = a.x_in[base + i];
-    }
-    // uncertainties on the final support: [K^-1]_rr = (G~_SS^-1)_rr - u_r^2 / (1^T G~_SS^-1 1)
-    if (a.sx_out) {
-        const double s = a.scale[0];
-        double w[KMAX];
-        int r = 0;
-        for (int i = 0; i < P; ++i) {
-            float out = 0.f;
-            if (r < k && idx[r] == i) {
-                // column r of L^-1: w_r = 1/L_rr, w_m = -(sum_{q=r}^{m-1} L_mq w_q)/L_mm
-                double dinv = 0.0;
-                for (int m = r; m < k; ++m) {
-                    double sacc = (m == r) ? 1.0 : 0.0;
-                    for (int q = r; q < m; ++q) sacc -= mat(m, q) * w[q];
-                    w[m] = sacc * mat(m, m);
-                    dinv += w[m] * w[m];
+        if (a.sx_out) {
+            const float s = (float)a.scale[0];
+            const df inv_a11 = df_div(df_make(1.f), a11);
+            df w[KMAX];
+            r = 0;
+            for (int i = 0; i < P; ++i) {
+                float out = 0.f;
+                if ((m >> i) & 1ULL) {
+                    // column r of L^-1: w_r = 1/L_rr, w_q = -(sum_{p=r}^{q-1} L_qp w_p)/L_qq
+                    df dinv = df_make(0.f);
+                    for (int q = r; q < k; ++q) {
+                        df sacc = df_make(q == r ? 1.f : 0.f);
+                        for (int p = r; p < q; ++p) sacc = df_fms(sacc, mat(q, p), w[p]);
+                        w[q] = df_mul(sacc, mat(q, q));
+                        dinv = df_add(dinv, df_mul(w[q], w[q]));
+                    }
+                    const df var = df_sub(dinv, df_mul(df_mul(u[r], u[r]), inv_a11));
+                    out = sqrtf(fmaxf(var.hi, 0.f) / s);
+                    ++r;
                 }
-                const double var = dinv - u[r] * u[r] / a11;
-                out = (float)sqrt(fmax(var, 0.0) / s);
-                ++r;
+                a.sx_out[base + i] = out;
             }
-            a.sx_out[base + i] = out;
         }
+        return;
     }
+    if (flip >= 0 && a.list_out) {
+        a.mask[n] = m ^ (1ULL << flip);
+        const unsigned long long pos = atomicAdd(a.len_out, 1ULL);
+        a.list_out[pos] = n;
+        return;
+    }
+    // not finished here: retry list, or (retry path) keep the iterate
+    if (a.retry_list) {
+        const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
+        a.retry_list[pos] = n;
+    } else if (a.n_unverified) {
+        atomicAdd(a.n_unverified, 1ULL);
+    }
+    if (a.x_out != a.x_in)
+        for (int i = 0; i < P; ++i) a.x_out[base + i] = a.x_in[base + i];
+    if (a.sx_out)
+        for (int i = 0; i < P; ++i) a.sx_out[base + i] = 0.f;
 }
 
 template <int KMAX>
-static cudaError_t launch_refine_t(const RefineArgs &a, cudaStream_t st)
+static cudaError_t launch_pass_t(const CrossArgs &a, cudaStream_t st)
 {
-    const size_t smem = sizeof(double) * (size_t)a.P * a.P;
-    cudaError_t e = cudaFuncSetAttribute(refine_kernel<KMAX>,
+    const size_t smem = 2 * sizeof(float) * (size_t)a.P * a.P;
+    cudaError_t e = cudaFuncSetAttribute(crossover_pass_kernel<KMAX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (a.N + REF_THREADS - 1) / REF_THREADS;   // list mode: <= N entries
-    refine_kernel<KMAX><<<(unsigned)blocks, REF_THREADS, smem, st>>>(a);
+    const long long blocks = (a.N + REF_THREADS - 1) / REF_THREADS;   // lists hold <= N entries
+    crossover_pass_kernel<KMAX><<<(unsigned)blocks, REF_THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_refine(const RefineArgs &a, cudaStream_t st)
+static cudaError_t launch_pass(const CrossArgs &a, cudaStream_t st)
 {
-    if (a.N <= 0) return cudaSuccess;
-    if (a.P <= 16) return launch_refine_t<16>(a, st);
-    if (a.P <= 32) return launch_refine_t<32>(a, st);
-    if (a.P <= 48) return launch_refine_t<48>(a, st);
-    return launch_refine_t<64>(a, st);
+    if (a.P <= 16) return launch_pass_t<16>(a, st);
+    if (a.P <= 32) return launch_pass_t<32>(a, st);
+    if (a.P <= 48) return launch_pass_t<48>(a, st);
+    return launch_pass_t<64>(a, st);
+}
+
+cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
+                             const long long *list, const unsigned long long *list_len,
+                             cudaStream_t st)
+{
+    if (base.N <= 0) return cudaSuccess;
+    const int T = 256;
+    const unsigned gridN = (unsigned)((base.N + T - 1) / T);
+    cudaError_t e;
+    // counters: w.len[0..MAX_SWAPS+1] list lengths, w.hist support-size counts
+    e = cudaMemsetAsync(w.len, 0, sizeof(unsigned long long) * (MAX_SWAPS + 2), st);
+    if (e != cudaSuccess) return e;
+    const long long *first = list;
+    const unsigned long long *first_len = list_len;
+    if (!list) {
+        // whole cube: counting sort by support size
+        e = cudaMemsetAsync(w.hist, 0, sizeof(unsigned int) * (base.P + 1), st);
+        if (e != cudaSuccess) return e;
+        support_kernel<<<gridN, T, 0, st>>>(base.N, base.P, base.x_in, base.lam_in, base.gdiag,
+                                             nullptr, nullptr, base.mask, w.ksize, w.hist);
+        bucket_scan_kernel<<<1, 32, 0, st>>>(base.P, w.hist, w.cursor, w.len_all);
+        bucket_scatter_kernel<<<gridN, T, 0, st>>>(base.N, w.ksize, w.cursor, w.list[0]);
+        first = w.list[0];
+        first_len = w.len_all;
+    } else {
+        support_kernel<<<gridN, T, 0, st>>>(base.N, base.P, base.x_in, base.lam_in, base.gdiag,
+                                             list, list_len, base.mask, w.ksize, nullptr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // pass p reads list (p & 1) (pass 0: the sorted list, or the given one)
+    // and writes list ((p + 1) & 1); the sorted list lives in w.list[0]
+    for (int pass = 0; pass <= MAX_SWAPS; ++pass) {
+        CrossArgs a = base;
+        a.list_in = pass == 0 ? first : w.list[pass & 1];
+        a.len_in = pass == 0 ? first_len : w.len + pass;
+        const bool last = pass == MAX_SWAPS;
+        a.list_out = last ? nullptr : w.list[(pass + 1) & 1];
+        a.len_out = last ? nullptr : w.len + pass + 1;
+        e = launch_pass(a, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------- rms

@@ -12,6 +12,11 @@ constexpr double RHO = 1.0;   // rho of G~ = G / s + rho 1 1^T (see ipm.cuh)
 // ~0.5 changes per pixel on average, at most a few).
 constexpr float MU_STOP = 1e-11f;
 constexpr int MAX_SWAPS = 8;
+// Initial support of the crossover: lambda_i < SUPPORT_THETA x_i G_ii.  A
+// threshold below 1 leaves the near-degenerate coordinates out (at mu/s =
+// 1e-11 they are the ones the crossover would drop again): ~10% of pixels
+// then need a support change instead of ~40% with 1.
+constexpr float SUPPORT_THETA = 0.01f;
 
 // Bucket of the interior-point kernel for a library size P.
 struct Bucket { int NS, G, PP; };
@@ -40,27 +45,45 @@ struct IpmArgs;
 cudaError_t launch_ipm(const Bucket &b, bool accurate, const IpmArgs &a,
                        cudaStream_t st);
 
-struct RefineArgs {
+struct CrossArgs {
     long long N;
     int P;
-    const double *Gt64;            // P x P
-    const float *Ghi, *Glo;        // PP x PP, G~ as hi + lo float32
+    const double *Gt64;            // P x P   G~ (fp64)
+    const float *Ghi, *Glo;        // PP x PP G~ as hi + lo float32
     int PP;
-    const double *scale;
-    const float *gdiag;            // P
+    const double *scale;           // s
+    const float *gdiag;            // P       diag(G) / s
     const float *c_hi, *c_lo;      // N x P
-    const float *x_in, *lam_in;    // N x P (interior-point result)
-    float *x_out;                  // N x P (may alias x_in)
+    const float *x_in, *lam_in;    // N x P   interior-point iterate
+    float *x_out;                  // N x P   (may alias x_in)
     float *sx_out;                 // N x P or NULL
-    unsigned long long *n_unverified;   // pixels whose crossover did not reach KKT
-    double tol_x, tol_g;
-    int max_swaps;                 // support changes allowed before giving up
-    const long long *list;         // optional: pixels to process (else 0..N-1)
-    const unsigned long long *list_len;
-    long long *retry_list;         // optional: pixels that failed, appended
+    unsigned long long *mask;      // N       support bit masks (in/out)
+    const long long *list_in;      // pixels of this pass
+    const unsigned long long *len_in;
+    long long *list_out;           // pixels handed to the next pass
+    unsigned long long *len_out;
+    long long *retry_list;         // pixels the crossover could not finish (or NULL)
     unsigned long long *retry_len;
+    unsigned long long *n_unverified;   // counted when retry_list is NULL
+    double tol_x, tol_g;
 };
-cudaError_t launch_refine(const RefineArgs &a, cudaStream_t st);
+
+// Device scratch of the crossover: two ping-pong pixel lists, per-pass
+// list lengths, the support-size histogram and bucket cursors.
+struct CrossoverScratch {
+    long long *list[2];            // N each
+    unsigned long long *len;       // MAX_SWAPS + 2
+    unsigned long long *len_all;   // 1
+    unsigned long long *cursor;    // P + 1
+    unsigned int *hist;            // P + 1
+    int *ksize;                    // N
+};
+
+// Crossover of the pixels in list (or of all N pixels, sorted by support
+// size, when list is NULL): up to MAX_SWAPS + 1 passes.
+cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
+                             const long long *list, const unsigned long long *list_len,
+                             cudaStream_t st);
 
 cudaError_t launch_rms(const float *cube, const float *S, const float *x,
                        long long N, int L, int P, float *rms, cudaStream_t st);

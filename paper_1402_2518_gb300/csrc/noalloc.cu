@@ -74,10 +74,18 @@ size_t scratch_needed(int L, int P, int PP, long long N)
     c.take<float>((size_t)L * PQ);
     c.take<int>(1);
     c.take<unsigned long long>(8);
+    c.take<unsigned long long>(MAX_SWAPS + 2);
+    c.take<unsigned long long>(1);
+    c.take<unsigned long long>(P + 1);
+    c.take<unsigned int>(P + 1);
     for (int k = 0; k < 4; ++k) c.take<float>((size_t)N * P);
     c.take<float>(N);
     c.take<int>(N);
     c.take<long long>(N);
+    c.take<unsigned long long>(N);
+    c.take<long long>(N);
+    c.take<long long>(N);
+    c.take<int>(N);
     return c.off;
 }
 
@@ -126,6 +134,11 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     pr.Blo = c.take<float>((size_t)L * PQ);
     pr.flags = c.take<int>(1);
     unsigned long long *cnt = c.take<unsigned long long>(8);
+    CrossoverScratch xw;
+    xw.len = c.take<unsigned long long>(MAX_SWAPS + 2);
+    xw.len_all = c.take<unsigned long long>(1);
+    xw.cursor = c.take<unsigned long long>(P + 1);
+    xw.hist = c.take<unsigned int>(P + 1);
     float *c_hi = c.take<float>((size_t)N * P);
     float *c_lo = c.take<float>((size_t)N * P);
     float *xs = c.take<float>((size_t)N * P);
@@ -133,6 +146,10 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     float *nu = c.take<float>(N);
     int *its = c.take<int>(N);
     long long *retry = c.take<long long>(N);
+    unsigned long long *mask = c.take<unsigned long long>(N);
+    xw.list[0] = c.take<long long>(N);
+    xw.list[1] = c.take<long long>(N);
+    xw.ksize = c.take<int>(N);
 
 #define NA_CUDA(call)                                  \
     do {                                               \
@@ -156,22 +173,20 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     ia.mu_ref = MU_STOP; ia.counter = cnt + 0;
     NA_CUDA(launch_ipm(b, false, ia, st));
     float *x_out = abundances ? abundances : xs;
-    RefineArgs ra;
-    ra.N = N; ra.P = P; ra.Gt64 = pr.Gt64; ra.scale = pr.scale; ra.gdiag = pr.gdiag;
-    ra.Ghi = pr.Ghi; ra.Glo = pr.Glo; ra.PP = PP;
-    ra.c_hi = c_hi; ra.c_lo = c_lo; ra.x_in = xs; ra.lam_in = lam;
-    ra.x_out = x_out; ra.sx_out = uncertainties; ra.n_unverified = cnt + 6;
-    ra.tol_x = 1e-9; ra.tol_g = 1e-9; ra.max_swaps = MAX_SWAPS;
-    ra.list = nullptr; ra.list_len = nullptr; ra.retry_list = retry; ra.retry_len = cnt + 5;
-    NA_CUDA(launch_refine(ra, st));
+    CrossArgs ca{};
+    ca.N = N; ca.P = P; ca.Gt64 = pr.Gt64; ca.Ghi = pr.Ghi; ca.Glo = pr.Glo; ca.PP = PP;
+    ca.scale = pr.scale; ca.gdiag = pr.gdiag; ca.c_hi = c_hi; ca.c_lo = c_lo;
+    ca.x_in = xs; ca.lam_in = lam; ca.x_out = x_out; ca.sx_out = uncertainties; ca.mask = mask;
+    ca.retry_list = retry; ca.retry_len = cnt + 5; ca.n_unverified = nullptr;
+    ca.tol_x = 1e-9; ca.tol_g = 1e-9;
+    NA_CUDA(launch_crossover(ca, xw, nullptr, nullptr, st));
     ia.list = retry; ia.list_len = cnt + 5;
     ia.mu_ref = o.refine_mu; ia.counter = cnt + 1;
     NA_CUDA(launch_ipm(b, false, ia, st));
     ia.counter = cnt + 4;
     NA_CUDA(launch_ipm(b, true, ia, st));
-    ra.list = retry; ra.list_len = cnt + 5;
-    ra.retry_list = nullptr; ra.retry_len = nullptr; ra.n_unverified = cnt + 3;
-    NA_CUDA(launch_refine(ra, st));
+    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = cnt + 3;
+    NA_CUDA(launch_crossover(ca, xw, retry, cnt + 5, st));
     if (residual_rms) NA_CUDA(launch_rms(cube, library, x_out, N, L, P, residual_rms, st));
     if (iterations)
         NA_CUDA(cudaMemcpyAsync(iterations, its, (size_t)N * sizeof(int),

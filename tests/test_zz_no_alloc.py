@@ -67,7 +67,7 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     sig = torch.from_numpy(cube.sigma).to(dev)
     X = torch.from_numpy(cube.X).to(dev)
     # N far beyond what LINMIN_NOALLOC_SCRATCH_MB can hold: refused before any work
-    too_many = (linmin.LINMIN_NOALLOC_SCRATCH_MB << 20) // (4 * (4 * cube.P + 4)) + 1
+    too_many = (linmin.LINMIN_NOALLOC_SCRATCH_MB << 20) // (4 * (4 * cube.P + 11)) + 1
     assert pkg.linmin_unmix_noalloc(S, cube.L, cube.P, X, too_many, sig) == linmin.LINMIN_ERR_INVALID
     # host buffers are refused (the entry point cannot stage them)
     x_host = np.empty((64, cube.P), np.float32)
