@@ -227,21 +227,23 @@ __global__ void support_kernel(long long N, int P, const float *__restrict__ x,
     if (hist) atomicAdd(hist + kk, 1u);
 }
 
-// Exclusive prefix sum of the P+1 support-size counts (one block); *total
-// receives the number of listed pixels.
+// Bucket starts of the support sizes in decreasing order (one block): the
+// pixels with the largest supports, whose crossover is the longest serial
+// computation, are listed first and start first; *total receives the
+// number of listed pixels.
 __global__ void bucket_scan_kernel(int P, const unsigned int *__restrict__ hist,
                                    unsigned long long *__restrict__ cursor,
                                    unsigned long long *__restrict__ total)
 {
     if (threadIdx.x == 0) {
         unsigned long long s = 0;
-        for (int kk = 0; kk <= P; ++kk) { cursor[kk] = s; s += hist[kk]; }
+        for (int kk = P; kk >= 0; --kk) { cursor[kk] = s; s += hist[kk]; }
         *total = s;
     }
 }
 
-// Pixels listed by increasing support size (counting sort), so that the
-// lanes of a warp run the O(k^3) crossover loops to similar k.
+// Pixels listed by support size (counting sort), so that the lanes of a
+// warp run the O(k^3) crossover loops to similar k.
 __global__ void bucket_scatter_kernel(long long N, const int *__restrict__ ksize,
                                       unsigned long long *__restrict__ cursor,
                                       long long *__restrict__ list)
@@ -293,39 +295,69 @@ crossover_pass_kernel(const CrossArgs a)
     auto mat = [&](int r, int c) -> df & { return M[r * (r + 1) / 2 + c]; };
     auto gt = [&](int i, int j) -> df { return df{sGh[i * P + j], sGl[i * P + j]}; };
 
-    // Cholesky of G~_SS; the diagonal keeps 1 / L_cc
+    // Cholesky of G~_SS (left-looking by columns); the diagonal keeps 1/L_cc.
+    // The dot products of a column are independent across rows: four rows
+    // run together so that four double-float chains are in flight.
     for (int r = 0; r < k; ++r)
         for (int c = 0; c <= r; ++c) mat(r, c) = gt(idx[r], idx[c]);
     bool fact_ok = true;
+    const df zero = df_make(0.f);
     for (int c = 0; c < k; ++c) {
-        df d = mat(c, c);
-        for (int q = 0; q < c; ++q) d = df_fms(d, mat(c, q), mat(c, q));
+        df d0 = mat(c, c), d1 = zero;
+        int q = 0;
+        for (; q + 1 < c; q += 2) {
+            d0 = df_fms(d0, mat(c, q), mat(c, q));
+            d1 = df_fms(d1, mat(c, q + 1), mat(c, q + 1));
+        }
+        if (q < c) d0 = df_fms(d0, mat(c, q), mat(c, q));
+        df d = df_add(d0, d1);
         if (!(d.hi > 0.f)) { fact_ok = false; d = df_make(1e-30f); }
         const df rl = df_rsqrt(d);
         mat(c, c) = rl;
-        for (int r = c + 1; r < k; ++r) {
-            df sacc = mat(r, c);
-            for (int q = 0; q < c; ++q) sacc = df_fms(sacc, mat(r, q), mat(c, q));
-            mat(r, c) = df_mul(sacc, rl);
+        for (int r = c + 1; r < k; r += 4) {
+            const int r1 = min(r + 1, k - 1), r2 = min(r + 2, k - 1), r3 = min(r + 3, k - 1);
+            df s0 = mat(r, c), s1 = mat(r1, c), s2 = mat(r2, c), s3 = mat(r3, c);
+            for (int p = 0; p < c; ++p) {
+                const df mc = mat(c, p);
+                s0 = df_fms(s0, mat(r, p), mc);
+                s1 = df_fms(s1, mat(r1, p), mc);
+                s2 = df_fms(s2, mat(r2, p), mc);
+                s3 = df_fms(s3, mat(r3, p), mc);
+            }
+            mat(r, c) = df_mul(s0, rl);
+            if (r + 1 < k) mat(r1, c) = df_mul(s1, rl);
+            if (r + 2 < k) mat(r2, c) = df_mul(s2, rl);
+            if (r + 3 < k) mat(r3, c) = df_mul(s3, rl);
         }
     }
-    // forward: u = L^-1 1, v = L^-1 c~_S
+    // forward: u = L^-1 1, v = L^-1 c~_S (two independent chains, each
+    // split in even/odd partial sums)
     for (int r = 0; r < k; ++r) {
-        df su = df_make(1.f);
-        df sv = df{a.c_hi[base + idx[r]], a.c_lo[base + idx[r]]};
-        for (int q = 0; q < r; ++q) { su = df_fms(su, mat(r, q), u[q]); sv = df_fms(sv, mat(r, q), v[q]); }
-        u[r] = df_mul(su, mat(r, r));
-        v[r] = df_mul(sv, mat(r, r));
+        df su0 = df_make(1.f), su1 = zero;
+        df sv0 = df{a.c_hi[base + idx[r]], a.c_lo[base + idx[r]]}, sv1 = zero;
+        int q = 0;
+        for (; q + 1 < r; q += 2) {
+            su0 = df_fms(su0, mat(r, q), u[q]); sv0 = df_fms(sv0, mat(r, q), v[q]);
+            su1 = df_fms(su1, mat(r, q + 1), u[q + 1]); sv1 = df_fms(sv1, mat(r, q + 1), v[q + 1]);
+        }
+        if (q < r) { su0 = df_fms(su0, mat(r, q), u[q]); sv0 = df_fms(sv0, mat(r, q), v[q]); }
+        u[r] = df_mul(df_add(su0, su1), mat(r, r));
+        v[r] = df_mul(df_add(sv0, sv1), mat(r, r));
     }
-    df a11 = df_make(0.f), a1b = df_make(0.f);
+    df a11 = zero, a1b = zero;
     for (int r = 0; r < k; ++r) { a11 = df_add(a11, df_mul(u[r], u[r])); a1b = df_add(a1b, df_mul(u[r], v[r])); }
     const df nu = df_div(df_sub(a1b, df_make(1.f)), a11);
     // back: xs = L^-T (v - nu u), u <- L^-T u (= G~_SS^-1 1)
     for (int r = k - 1; r >= 0; --r) {
-        df sx = df_fms(v[r], nu, u[r]), su = u[r];
-        for (int q = r + 1; q < k; ++q) { sx = df_fms(sx, mat(q, r), xs[q]); su = df_fms(su, mat(q, r), u[q]); }
-        xs[r] = df_mul(sx, mat(r, r));
-        u[r] = df_mul(su, mat(r, r));
+        df sx0 = df_fms(v[r], nu, u[r]), su0 = u[r], sx1 = zero, su1 = zero;
+        int q = r + 1;
+        for (; q + 1 < k; q += 2) {
+            sx0 = df_fms(sx0, mat(q, r), xs[q]); su0 = df_fms(su0, mat(q, r), u[q]);
+            sx1 = df_fms(sx1, mat(q + 1, r), xs[q + 1]); su1 = df_fms(su1, mat(q + 1, r), u[q + 1]);
+        }
+        if (q < k) { sx0 = df_fms(sx0, mat(q, r), xs[q]); su0 = df_fms(su0, mat(q, r), u[q]); }
+        xs[r] = df_mul(df_add(sx0, sx1), mat(r, r));
+        u[r] = df_mul(df_add(su0, su1), mat(r, r));
     }
     // decision
     int flip = -1;             // coordinate whose membership in S changes
@@ -338,20 +370,34 @@ crossover_pass_kernel(const CrossArgs a)
         }
         if (flip >= 0 && k == 1) flip = -2;       // cannot drop the last one
         if (flip == -1) {
-            // most negative multiplier off S
+            // most negative multiplier off S; four coordinates at once
             float lmin = (float)-a.tol_g;
-            for (int i = 0; i < P; ++i) {
-                if ((m >> i) & 1ULL) continue;
-                dot2 g;
+            int off[KMAX];
+            int noff = 0;
+            for (int i = 0; i < P; ++i)
+                if (!((m >> i) & 1ULL)) off[noff++] = i;
+            for (int o = 0; o < noff; o += 4) {
+                int ii[4];
+                dot2 g[4];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) ii[w] = off[min(o + w, noff - 1)];
                 for (int q = 0; q < k; ++q) {
-                    const float gh = sGh[i * P + idx[q]], gl = sGl[i * P + idx[q]];
-                    g.add_prod(gh, xs[q].hi);
-                    g.c = fmaf(gh, xs[q].lo, fmaf(gl, xs[q].hi, g.c));
+                    const float xh = xs[q].hi, xl = xs[q].lo;
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const float gh = sGh[ii[w] * P + idx[q]], gl = sGl[ii[w] * P + idx[q]];
+                        g[w].add_prod(gh, xh);
+                        g[w].c = fmaf(gh, xl, fmaf(gl, xh, g[w].c));
+                    }
                 }
-                g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
-                g.add_df(nu);
-                const df gv = g.result();
-                if (gv.hi < lmin) { lmin = gv.hi; flip = i; }
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    if (o + w >= noff) break;
+                    g[w].add_df(df{-a.c_hi[base + ii[w]], -a.c_lo[base + ii[w]]});
+                    g[w].add_df(nu);
+                    const df gv = g[w].result();
+                    if (gv.hi < lmin) { lmin = gv.hi; flip = ii[w]; }
+                }
             }
         }
     } else {
@@ -368,20 +414,33 @@ crossover_pass_kernel(const CrossArgs a)
         if (a.sx_out) {
             const float s = (float)a.scale[0];
             const df inv_a11 = df_div(df_make(1.f), a11);
-            df w[KMAX];
-            r = 0;
+            // diag of G~_SS^-1 = column norms of L^-1: w = L^-1 e_r by forward
+            // substitution from row r; two columns at a time
+            df dsq[KMAX];
+            for (int r0 = 0; r0 < k; r0 += 2) {
+                const int r1 = min(r0 + 1, k - 1);
+                df w0[KMAX], w1[KMAX];
+                df n0 = zero, n1 = zero;
+                for (int q = r0; q < k; ++q) {
+                    df s0 = df_make(q == r0 ? 1.f : 0.f), s1 = df_make(q == r1 ? 1.f : 0.f);
+                    for (int p = r0; p < q; ++p) {
+                        const df lqp = mat(q, p);
+                        s0 = df_fms(s0, lqp, w0[p]);
+                        s1 = df_fms(s1, lqp, p >= r1 ? w1[p] : zero);
+                    }
+                    w0[q] = df_mul(s0, mat(q, q));
+                    w1[q] = q >= r1 ? df_mul(s1, mat(q, q)) : zero;
+                    n0 = df_add(n0, df_mul(w0[q], w0[q]));
+                    n1 = df_add(n1, df_mul(w1[q], w1[q]));
+                }
+                dsq[r0] = n0;
+                if (r0 + 1 < k) dsq[r1] = n1;
+            }
+            int r = 0;
             for (int i = 0; i < P; ++i) {
                 float out = 0.f;
                 if ((m >> i) & 1ULL) {
-                    // column r of L^-1: w_r = 1/L_rr, w_q = -(sum_{p=r}^{q-1} L_qp w_p)/L_qq
-                    df dinv = df_make(0.f);
-                    for (int q = r; q < k; ++q) {
-                        df sacc = df_make(q == r ? 1.f : 0.f);
-                        for (int p = r; p < q; ++p) sacc = df_fms(sacc, mat(q, p), w[p]);
-                        w[q] = df_mul(sacc, mat(q, q));
-                        dinv = df_add(dinv, df_mul(w[q], w[q]));
-                    }
-                    const df var = df_sub(dinv, df_mul(df_mul(u[r], u[r]), inv_a11));
+                    const df var = df_sub(dsq[r], df_mul(df_mul(u[r], u[r]), inv_a11));
                     out = sqrtf(fmaxf(var.hi, 0.f) / s);
                     ++r;
                 }
