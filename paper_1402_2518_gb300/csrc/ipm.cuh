@@ -41,13 +41,11 @@
 
 namespace lm {
 
-constexpr int IPM_WARPS = 4;
 
 // Compiler-only memory fence: keeps the scheduler from hoisting the shared
 // memory loads of later unrolled steps (which would hold them all in
 // registers at once).
 #define LM_STEP_FENCE() asm volatile("" ::: "memory")
-constexpr int IPM_THREADS = IPM_WARPS * 32;
 
 struct IpmArgs {
     long long N;
@@ -74,6 +72,8 @@ struct IpmCfg {
     // resident blocks per SM the register budget is sized for: 9 slots of
     // 4 lanes hold 180 registers of H per lane, so 2 blocks; others 3
     static constexpr int MIN_BLOCKS = NS >= 8 ? 2 : 3;
+    static constexpr int WARPS = 4;       // warps per block
+    static constexpr int THREADS = WARPS * 32;
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
     static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
     static constexpr __host__ __device__ int collen(int k) { return PP - alignrow(k); }
@@ -90,12 +90,12 @@ struct IpmCfg {
     static constexpr int GROUP_FLOATS = ((GROUP_RAW + 31) / 32) * 32 + 4;
     static constexpr size_t smem_bytes(bool acc) {
         return sizeof(float) * ((acc ? 2 : 1) * PP * PP + PP +
-                                (size_t)IPM_WARPS * GPW * GROUP_FLOATS);
+                                (size_t)WARPS * GPW * GROUP_FLOATS);
     }
 };
 
 template <int NS, int G, bool ACC>
-__global__ void __launch_bounds__(IPM_THREADS, IpmCfg<NS, G>::MIN_BLOCKS)
+__global__ void __launch_bounds__(IpmCfg<NS, G>::THREADS, IpmCfg<NS, G>::MIN_BLOCKS)
 ipm_kernel(const IpmArgs a)
 {
     using C = IpmCfg<NS, G>;
@@ -200,7 +200,7 @@ ipm_kernel(const IpmArgs a)
             float acc[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) acc[s] = 0.f;
-#pragma unroll
+#pragma unroll 1
             for (int j4 = 0; j4 < PP / 4; ++j4) {
                 const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
 #pragma unroll
@@ -432,55 +432,62 @@ ipm_kernel(const IpmArgs a)
             }
         };
 
-        // ---- predictor (affine scaling direction)
+        // ---- predictor (affine scaling direction) and corrector.  The two
+        // back solves share one copy of their (unrolled) code: a two-trip
+        // loop kept rolled, which halves that part of the loop body and its
+        // instruction-cache footprint.
         float p11 = 0.f, p1a = 0.f;
 #pragma unroll
         for (int s = 0; s < NS; ++s) { p11 = fmaf(B1[s], B1[s], p11); p1a = fmaf(B1[s], B2[s], p1a); }
         const float a11 = group_sum(p11, G);
         const float a1a = group_sum(p1a, G);
         const float dnu_a = (a1a + rp) / a11;
-        float dxa[NS], dla[NS];
+        float dxa[NS], corr[NS], dnu_c = 0.f, ap = 1.f, ad = 1.f;
+        float v[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) dxa[s] = fmaf(-dnu_a, B1[s], B2[s]);
-        back_solve(dxa);
-        float ap = 1.f, ad = 1.f;
+        for (int s = 0; s < NS; ++s) { v[s] = fmaf(-dnu_a, B1[s], B2[s]); corr[s] = 0.f; dxa[s] = 0.f; }
+#pragma unroll 1
+        for (int trip = 0; trip < 2; ++trip) {
+            back_solve(v);
+            if (trip == 1) break;
+            // affine step: dlam_aff, step lengths, mu_aff, centering sigma
+            float dla[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            dla[s] = valid[s] ? fmaf(-Dof(s), dxa[s], -lam[s]) : 0.f;
-            if (valid[s] && dxa[s] < 0.f) ap = fminf(ap, __fdividef(-x[s], dxa[s]));
-            if (valid[s] && dla[s] < 0.f) ad = fminf(ad, __fdividef(-lam[s], dla[s]));
+            for (int s = 0; s < NS; ++s) {
+                dxa[s] = v[s];
+                dla[s] = valid[s] ? fmaf(-Dof(s), dxa[s], -lam[s]) : 0.f;
+                if (valid[s] && dxa[s] < 0.f) ap = fminf(ap, __fdividef(-x[s], dxa[s]));
+                if (valid[s] && dla[s] < 0.f) ad = fminf(ad, __fdividef(-lam[s], dla[s]));
+            }
+            ap = group_min(ap, G);
+            ad = group_min(ad, G);
+            float pma = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) pma = fmaf(fmaf(ap, dxa[s], x[s]), fmaf(ad, dla[s], lam[s]), pma);
+            const float mua = group_sum(pma, G) * invP;
+            float sig = (mu > 0.f) ? mua / mu : 0.f;
+            sig = fminf(sig * sig * sig, 1.f);
+            const float smu = sig * mu;
+            // corrector right-hand side -X^-1 (dx_aff o dlam_aff - sigma mu 1)
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                corr[s] = valid[s] ? __fdividef(fmaf(dxa[s], dla[s], -smu), x[s]) : 0.f;
+                v[s] = -corr[s];
+            }
+            fwd_solve(v);
+            float p1c = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) p1c = fmaf(B1[s], v[s], p1c);
+            dnu_c = group_sum(p1c, G) / a11;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) v[s] = fmaf(-dnu_c, B1[s], v[s]);
         }
-        ap = group_min(ap, G);
-        ad = group_min(ad, G);
-        float pma = 0.f;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) pma = fmaf(fmaf(ap, dxa[s], x[s]), fmaf(ad, dla[s], lam[s]), pma);
-        const float mua = group_sum(pma, G) * invP;
-        float sig = (mu > 0.f) ? mua / mu : 0.f;
-        sig = fminf(sig * sig * sig, 1.f);
-        const float smu = sig * mu;
-
-        // ---- corrector: rhs -X^-1 (dx_aff o dlam_aff - sigma mu 1)
-        float corr[NS], zc[NS];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            corr[s] = valid[s] ? __fdividef(fmaf(dxa[s], dla[s], -smu), x[s]) : 0.f;
-            zc[s] = -corr[s];
-        }
-        fwd_solve(zc);
-        float p1c = 0.f;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) p1c = fmaf(B1[s], zc[s], p1c);
-        const float dnu_c = group_sum(p1c, G) / a11;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) zc[s] = fmaf(-dnu_c, B1[s], zc[s]);
-        back_solve(zc);
 
         float dx[NS], dl[NS];
         ap = 1.f; ad = 1.f;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            dx[s] = dxa[s] + zc[s];
+            dx[s] = dxa[s] + v[s];
             dl[s] = valid[s] ? fmaf(-Dof(s), dx[s], -lam[s] - corr[s]) : 0.f;
             if (valid[s] && dx[s] < 0.f) ap = fminf(ap, __fdividef(-x[s], dx[s]));
             if (valid[s] && dl[s] < 0.f) ad = fminf(ad, __fdividef(-lam[s], dl[s]));

@@ -17,14 +17,14 @@ cudaError_t launch_ipm_mode(const IpmArgs &a, cudaStream_t st)
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ipm_kernel<NS, G, ACC>, IPM_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ipm_kernel<NS, G, ACC>, C::THREADS, smem);
     if (per_sm < 1) per_sm = 1;
     // persistent grid: one wave of resident blocks, capped by the pixel count
-    const long long groups_per_block = (long long)IPM_WARPS * C::GPW;
+    const long long groups_per_block = (long long)C::WARPS * C::GPW;
     long long blocks = (long long)nsm * per_sm;
     const long long need = (a.N + groups_per_block - 1) / groups_per_block;
     if (blocks > need) blocks = need;
-    ipm_kernel<NS, G, ACC><<<(unsigned)blocks, IPM_THREADS, smem, st>>>(a);
+    ipm_kernel<NS, G, ACC><<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
     return cudaGetLastError();
 }
 
