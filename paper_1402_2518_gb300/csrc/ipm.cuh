@@ -325,48 +325,68 @@ ipm_kernel(const IpmArgs a)
             B1[s] = valid[s] ? 1.f : 0.f;
             B2[s] = -rd[s] - lam[s];
         }
+        // Column k = sk*G + tk: the slot block sk is unrolled (register
+        // indices of H stay compile-time), the G columns of a block share one
+        // copy of the code (rolled loop over tk, column picked by selects).
+        // The loop body is then about 1/G of the fully unrolled one: the
+        // kernel is bound by instruction fetch, not by the extra selects.
 #pragma unroll
-        for (int k = 0; k < PP; ++k) {
-            const int sk = k / G, tk = k % G;
-            float d = __shfl_sync(FULL, H[sk][k], tk, G);
-            d = (d > TINY) ? d : BIGPIV;
-            const float r = rsqrtf(d);
+        for (int sk = 0; sk < NS; ++sk) {
+#pragma unroll 1
+            for (int tk = 0; tk < G; ++tk) {
+                const int k = sk * G + tk;
+                float hk[NS];
 #pragma unroll
-            for (int s = sk; s < NS; ++s) {
-                const bool below = (s > sk) || (t > tk);
-                if (below) {
-                    H[s][k] *= r;
-                    colbuf[C::colstart(k) + s * G + t - C::alignrow(k)] = H[s][k];
+                for (int s = sk; s < NS; ++s) {
+                    float h = H[s][sk * G];
+#pragma unroll
+                    for (int q = 1; q < G; ++q) h = (tk == q) ? H[s][sk * G + q] : h;
+                    hk[s] = h;
                 }
-            }
-            float z1 = 0.f, z2 = 0.f;
-            if (t == tk) {
-                dinv[sk] = r;                 // 1 / L_kk, kept by the row's owner
-                z1 = B1[sk] * r; z2 = B2[sk] * r;
-                B1[sk] = z1; B2[sk] = z2;
-            }
-            __syncwarp();
-            z1 = __shfl_sync(FULL, z1, tk, G);
-            z2 = __shfl_sync(FULL, z2, tk, G);
-            if (k + 1 < PP) {
+                float d = __shfl_sync(FULL, hk[sk], tk, G);
+                d = (d > TINY) ? d : BIGPIV;
+                const float r = rsqrtf(d);
+                float *col = colbuf + C::colstart(k) - C::alignrow(k);
                 float lik[NS];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    const bool below = (s > sk) || (t > tk);
-                    lik[s] = (s >= sk && below) ? H[s][k] : 0.f;
+                    const bool below = (s > sk) || (s == sk && t > tk);
+                    lik[s] = (s >= sk && below) ? hk[s] * r : 0.f;
+                    if (s >= sk && below) col[s * G + t] = lik[s];
                 }
+                float z1 = 0.f, z2 = 0.f;
+                if (t == tk) {
+                    dinv[sk] = r;                 // 1 / L_kk, kept by the row's owner
+                    z1 = B1[sk] * r; z2 = B2[sk] * r;
+                    B1[sk] = z1; B2[sk] = z2;
+                }
+                __syncwarp();
+                z1 = __shfl_sync(FULL, z1, tk, G);
+                z2 = __shfl_sync(FULL, z2, tk, G);
+                // columns of block sk right of k (runtime test j > k)
 #pragma unroll
-                for (int j4 = C::alignrow(k) / 4; j4 < PP / 4; ++j4) {
-                    const float4 lv = *reinterpret_cast<const float4 *>(
-                        colbuf + C::colstart(k) + 4 * j4 - C::alignrow(k));
+                for (int j4 = sk * G / 4; j4 < (sk + 1) * G / 4; ++j4) {
+                    const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
                     const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const int j = 4 * j4 + q;
-                        if (j <= k) continue;
+                        if (j > k) {
 #pragma unroll
-                        for (int s = sk; s < NS; ++s)
-                            if (j < (s + 1) * G) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
+                            for (int s = sk; s < NS; ++s) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
+                        }
+                    }
+                }
+                // columns of the later blocks (the bulk of the update)
+#pragma unroll
+                for (int j4 = (sk + 1) * G / 4; j4 < PP / 4; ++j4) {
+                    const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
+                    const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = 4 * j4 + q;
+#pragma unroll
+                        for (int s = j / G; s < NS; ++s) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
                     }
                 }
 #pragma unroll
@@ -375,18 +395,12 @@ ipm_kernel(const IpmArgs a)
                     B2[s] = fmaf(-lik[s], z2, B2[s]);
                 }
             }
-            LM_STEP_FENCE();
         }
         __syncwarp();
 
         // back solve L^T w = v in place (v distributed by rows); uses the
         // stored columns of L and 1/L_kk on each owner's diagonal
         auto back_solve = [&](float (&v)[NS]) {
-            // the loads of step k take their address from the value
-            // broadcast at step k+1 ((w == w) is 0 unless NaN), so the
-            // scheduler prefetches one step ahead instead of hoisting the
-            // loads of every step (which spills registers)
-            int dep = 0;
             int cb[NS];     // column i = s*G + t starts at cb[s] + alignrow(i)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
@@ -394,40 +408,43 @@ ipm_kernel(const IpmArgs a)
                 cb[s] = C::colstart(i) - C::alignrow(i);
             }
 #pragma unroll
-            for (int k = PP - 1; k >= 0; --k) {
-                const int sk = k / G, tk = k % G;
-                float lk[NS];
+            for (int sk = NS - 1; sk >= 0; --sk) {
+#pragma unroll 1
+                for (int tk = G - 1; tk >= 0; --tk) {
+                    const int k = sk * G + tk;
+                    float lk[NS];
 #pragma unroll
-                for (int s = 0; s <= sk; ++s) lk[s] = colbuf[cb[s] + k + dep];
-                float w = 0.f;
-                if (t == tk) { w = v[sk] * dinv[sk]; v[sk] = w; }
-                w = __shfl_sync(FULL, w, tk, G);
-                dep = (w == w) ? 0 : 1;
+                    for (int s = 0; s <= sk; ++s) lk[s] = colbuf[cb[s] + k];
+                    float w = 0.f;
+                    if (t == tk) { w = v[sk] * dinv[sk]; v[sk] = w; }
+                    w = __shfl_sync(FULL, w, tk, G);
 #pragma unroll
-                for (int s = 0; s <= sk; ++s) {
-                    const bool above = (s < sk) || (t < tk);
-                    if (above) v[s] = fmaf(-lk[s], w, v[s]);
+                    for (int s = 0; s <= sk; ++s) {
+                        const bool above = (s < sk) || (t < tk);
+                        if (above) v[s] = fmaf(-lk[s], w, v[s]);
+                    }
                 }
             }
         };
         // forward solve L z = b in place, L read from the stored columns
         auto fwd_solve = [&](float (&b)[NS]) {
-            int dep = 0;
 #pragma unroll
-            for (int k = 0; k < PP; ++k) {
-                const int sk = k / G, tk = k % G;
-                float lk[NS];
+            for (int sk = 0; sk < NS; ++sk) {
+#pragma unroll 1
+                for (int tk = 0; tk < G; ++tk) {
+                    const int k = sk * G + tk;
+                    const float *col = colbuf + C::colstart(k) - C::alignrow(k);
+                    float lk[NS];
 #pragma unroll
-                for (int s = sk; s < NS; ++s)
-                    lk[s] = colbuf[C::colstart(k) + s * G + t - C::alignrow(k) + dep];
-                float z = 0.f;
-                if (t == tk) { z = b[sk] * dinv[sk]; b[sk] = z; }
-                z = __shfl_sync(FULL, z, tk, G);
-                dep = (z == z) ? 0 : 1;
+                    for (int s = sk; s < NS; ++s) lk[s] = col[s * G + t];
+                    float z = 0.f;
+                    if (t == tk) { z = b[sk] * dinv[sk]; b[sk] = z; }
+                    z = __shfl_sync(FULL, z, tk, G);
 #pragma unroll
-                for (int s = sk; s < NS; ++s) {
-                    const bool below = (s > sk) || (t > tk);
-                    if (below) b[s] = fmaf(-lk[s], z, b[s]);
+                    for (int s = sk; s < NS; ++s) {
+                        const bool below = (s > sk) || (t > tk);
+                        if (below) b[s] = fmaf(-lk[s], z, b[s]);
+                    }
                 }
             }
         };
