@@ -262,34 +262,42 @@ ipm_kernel(const IpmArgs a)
     while (__syncthreads_or(alive)) {
         residual();
 
-        // ---- leave the active set / refill (per group); a warp in which a
-        // group refilled starts the trip again so that the new pixel gets its
-        // residual before its first Newton step
-        bool done;
-        if (!ACC) done = (mu <= a.mu_ref) || (it >= a.max_iter);
-        else done = ((rdmax <= a.tol_d) && (dec <= a.tol_c)) || (it >= a.max_iter);
-        done = done && alive;
-        if (done) {
-            const size_t base = (size_t)pix * P;
+        // ---- leave the active set / refill (per group).  A group whose
+        // pixel stopped stores it and takes the next one; the warp then
+        // recomputes the residual (unchanged for the other groups) and all
+        // groups take their Newton step in this same trip.  Each pass of the
+        // refill loop consumes work items, so it ends.
+        auto stop_test = [&]() -> bool {
+            bool d;
+            if (!ACC) d = (mu <= a.mu_ref) || (it >= a.max_iter);
+            else d = ((rdmax <= a.tol_d) && (dec <= a.tol_c)) || (it >= a.max_iter);
+            return d && alive;
+        };
+        bool done = stop_test();
+        while (__any_sync(FULL, done)) {
+            if (done) {
+                const size_t base = (size_t)pix * P;
 #pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                const int i = s * G + t;
-                if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
-            }
-            const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
-            if (t == 0) {
-                a.nu_state[pix] = nu;
-                if (!ACC) a.it_state[pix] = it;
-                else {
-                    a.it_state[pix] = conv ? it : -it;
-                    if (!conv) atomicAdd(a.n_notconv, 1ULL);
+                for (int s = 0; s < NS; ++s) {
+                    const int i = s * G + t;
+                    if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
                 }
+                const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
+                if (t == 0) {
+                    a.nu_state[pix] = nu;
+                    if (!ACC) a.it_state[pix] = it;
+                    else {
+                        a.it_state[pix] = conv ? it : -it;
+                        if (!conv) atomicAdd(a.n_notconv, 1ULL);
+                    }
+                }
+                pix = fetch();
+                alive = pix < a.N;
+                if (alive) load_pixel(pix);
             }
-            pix = fetch();
-            alive = pix < a.N;
-            if (alive) load_pixel(pix);
+            residual();
+            done = stop_test();
         }
-        if (__any_sync(FULL, done)) continue;
         if (!__any_sync(FULL, alive)) continue;
 
         // ---- barrier Hessian H = G~ + diag(lambda / x), lower rows in registers
