@@ -123,11 +123,14 @@ cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP
 // ------------------------------------------------------------ projection
 constexpr int PROJ_THREADS = 128;
 
+// Grid-stride over pixels (a persistent grid: B~ is staged in shared memory
+// once per block).  Four bands per step: one 16-byte load of the pixel's
+// row when rows are 16-byte aligned (vec), else four scalar loads.
 template <int NJ4>
 __global__ void __launch_bounds__(PROJ_THREADS)
 project_kernel(const float *__restrict__ cube, long long N, int L, int P,
                const float *__restrict__ Bhi, const float *__restrict__ Blo,
-               float *__restrict__ c_hi, float *__restrict__ c_lo)
+               float *__restrict__ c_hi, float *__restrict__ c_lo, bool vec)
 {
     constexpr int PQ = 4 * NJ4;
     extern __shared__ __align__(16) float sb[];
@@ -137,33 +140,59 @@ project_kernel(const float *__restrict__ cube, long long N, int L, int P,
         sBlo[e] = Blo[e];
     }
     __syncthreads();
-    const long long n = (long long)blockIdx.x * PROJ_THREADS + threadIdx.x;
-    if (n >= N) return;
-    dot2 acc[PQ];
-    const float *y = cube + (size_t)n * L;
-#pragma unroll 2
-    for (int l = 0; l < L; ++l) {
-        const float yl = __ldg(y + l);
-        const float *bh = sBhi + (size_t)l * PQ, *bl = sBlo + (size_t)l * PQ;
+    const long long stride = (long long)gridDim.x * PROJ_THREADS;
+    for (long long n = (long long)blockIdx.x * PROJ_THREADS + threadIdx.x; n < N; n += stride) {
+        dot2 acc[PQ];
+        const float *y = cube + (size_t)n * L;
+        auto band = [&](int l, float yl) {
+            const float *bh = sBhi + (size_t)l * PQ, *bl = sBlo + (size_t)l * PQ;
 #pragma unroll
-        for (int j4 = 0; j4 < NJ4; ++j4) {
-            const float4 h = *reinterpret_cast<const float4 *>(bh + 4 * j4);
-            const float4 o = *reinterpret_cast<const float4 *>(bl + 4 * j4);
-            acc[4 * j4 + 0].add_prod(h.x, yl); acc[4 * j4 + 0].c = fmaf(o.x, yl, acc[4 * j4 + 0].c);
-            acc[4 * j4 + 1].add_prod(h.y, yl); acc[4 * j4 + 1].c = fmaf(o.y, yl, acc[4 * j4 + 1].c);
-            acc[4 * j4 + 2].add_prod(h.z, yl); acc[4 * j4 + 2].c = fmaf(o.z, yl, acc[4 * j4 + 2].c);
-            acc[4 * j4 + 3].add_prod(h.w, yl); acc[4 * j4 + 3].c = fmaf(o.w, yl, acc[4 * j4 + 3].c);
+            for (int j4 = 0; j4 < NJ4; ++j4) {
+                const float4 h = *reinterpret_cast<const float4 *>(bh + 4 * j4);
+                const float4 o = *reinterpret_cast<const float4 *>(bl + 4 * j4);
+                acc[4 * j4 + 0].add_prod(h.x, yl); acc[4 * j4 + 0].c = fmaf(o.x, yl, acc[4 * j4 + 0].c);
+                acc[4 * j4 + 1].add_prod(h.y, yl); acc[4 * j4 + 1].c = fmaf(o.y, yl, acc[4 * j4 + 1].c);
+                acc[4 * j4 + 2].add_prod(h.z, yl); acc[4 * j4 + 2].c = fmaf(o.z, yl, acc[4 * j4 + 2].c);
+                acc[4 * j4 + 3].add_prod(h.w, yl); acc[4 * j4 + 3].c = fmaf(o.w, yl, acc[4 * j4 + 3].c);
+            }
+        };
+        int l = 0;
+        if (vec) {
+            for (; l + 4 <= L; l += 4) {
+                const float4 yv = __ldg(reinterpret_cast<const float4 *>(y + l));
+                band(l, yv.x); band(l + 1, yv.y); band(l + 2, yv.z); band(l + 3, yv.w);
+            }
+        }
+        for (; l < L; ++l) band(l, __ldg(y + l));
+#pragma unroll
+        for (int j = 0; j < PQ; ++j) {
+            if (j < P) {
+                acc[j].add_df(df{(float)RHO, 0.f});
+                const df r = acc[j].result();
+                c_hi[(size_t)n * P + j] = r.hi;
+                c_lo[(size_t)n * P + j] = r.lo;
+            }
         }
     }
-#pragma unroll
-    for (int j = 0; j < PQ; ++j) {
-        if (j < P) {
-            acc[j].add_df(df{(float)RHO, 0.f});
-            const df r = acc[j].result();
-            c_hi[(size_t)n * P + j] = r.hi;
-            c_lo[(size_t)n * P + j] = r.lo;
-        }
-    }
+}
+
+// one wave of resident blocks (at most one block per 128 pixels)
+template <typename K>
+static unsigned persistent_blocks(K kernel, int threads, size_t smem, long long N)
+{
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    const long long need = (N + threads - 1) / threads;
+    const long long wave = (long long)sms * per_sm;
+    return (unsigned)(need < wave ? need : wave);
+}
+
+static bool rows_aligned(const float *cube, int L)
+{
+    return (L % 4) == 0 && (reinterpret_cast<uintptr_t>(cube) % 16) == 0;
 }
 
 template <int NJ4>
@@ -175,9 +204,9 @@ static cudaError_t launch_project_t(const float *cube, long long N, int L, int P
     cudaError_t e = cudaFuncSetAttribute(project_kernel<NJ4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (N + PROJ_THREADS - 1) / PROJ_THREADS;
-    project_kernel<NJ4><<<(unsigned)blocks, PROJ_THREADS, smem, st>>>(cube, N, L, P, Bhi, Blo,
-                                                                       c_hi, c_lo);
+    const unsigned blocks = persistent_blocks(project_kernel<NJ4>, PROJ_THREADS, smem, N);
+    project_kernel<NJ4><<<blocks, PROJ_THREADS, smem, st>>>(cube, N, L, P, Bhi, Blo, c_hi, c_lo,
+                                                            rows_aligned(cube, L));
     return cudaGetLastError();
 }
 
@@ -535,10 +564,14 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
 // ------------------------------------------------------------------- rms
 constexpr int RMS_THREADS = 128;
 
+// Grid-stride over pixels, thread per pixel, S^T staged in shared memory
+// once per block; four bands per step (four independent chains over the
+// library, one 16-byte load of the row when rows are 16-byte aligned).
 template <int NJ4>
 __global__ void __launch_bounds__(RMS_THREADS)
 rms_kernel(const float *__restrict__ cube, const float *__restrict__ S,
-           const float *__restrict__ x, long long N, int L, int P, float *__restrict__ rms)
+           const float *__restrict__ x, long long N, int L, int P, float *__restrict__ rms,
+           bool vec)
 {
     constexpr int PQ = 4 * NJ4;
     extern __shared__ __align__(16) float st[];   // [l][PQ] = S^T, zero padded
@@ -547,28 +580,42 @@ rms_kernel(const float *__restrict__ cube, const float *__restrict__ S,
         st[e] = j < P ? S[(size_t)j * L + l] : 0.f;
     }
     __syncthreads();
-    const long long n = (long long)blockIdx.x * RMS_THREADS + threadIdx.x;
-    if (n >= N) return;
-    float xv[PQ];
+    const long long stride = (long long)gridDim.x * RMS_THREADS;
+    for (long long n = (long long)blockIdx.x * RMS_THREADS + threadIdx.x; n < N; n += stride) {
+        float xv[PQ];
 #pragma unroll
-    for (int j = 0; j < PQ; ++j) xv[j] = j < P ? x[(size_t)n * P + j] : 0.f;
-    const float *y = cube + (size_t)n * L;
-    float acc = 0.f;
-    for (int l = 0; l < L; ++l) {
-        float m = 0.f;
-        const float *row = st + (size_t)l * PQ;
+        for (int j = 0; j < PQ; ++j) xv[j] = j < P ? x[(size_t)n * P + j] : 0.f;
+        const float *y = cube + (size_t)n * L;
+        auto fit = [&](int l) {
+            const float *row = st + (size_t)l * PQ;
+            float m = 0.f;
 #pragma unroll
-        for (int j4 = 0; j4 < NJ4; ++j4) {
-            const float4 sv = *reinterpret_cast<const float4 *>(row + 4 * j4);
-            m = fmaf(xv[4 * j4 + 0], sv.x, m);
-            m = fmaf(xv[4 * j4 + 1], sv.y, m);
-            m = fmaf(xv[4 * j4 + 2], sv.z, m);
-            m = fmaf(xv[4 * j4 + 3], sv.w, m);
+            for (int j4 = 0; j4 < NJ4; ++j4) {
+                const float4 sv = *reinterpret_cast<const float4 *>(row + 4 * j4);
+                m = fmaf(xv[4 * j4 + 0], sv.x, m);
+                m = fmaf(xv[4 * j4 + 1], sv.y, m);
+                m = fmaf(xv[4 * j4 + 2], sv.z, m);
+                m = fmaf(xv[4 * j4 + 3], sv.w, m);
+            }
+            return m;
+        };
+        float acc0 = 0.f, acc1 = 0.f;
+        int l = 0;
+        if (vec) {
+            for (; l + 4 <= L; l += 4) {
+                const float4 yv = __ldg(reinterpret_cast<const float4 *>(y + l));
+                const float e0 = yv.x - fit(l), e1 = yv.y - fit(l + 1);
+                const float e2 = yv.z - fit(l + 2), e3 = yv.w - fit(l + 3);
+                acc0 = fmaf(e0, e0, acc0); acc1 = fmaf(e1, e1, acc1);
+                acc0 = fmaf(e2, e2, acc0); acc1 = fmaf(e3, e3, acc1);
+            }
         }
-        const float e = __ldg(y + l) - m;
-        acc = fmaf(e, e, acc);
+        for (; l < L; ++l) {
+            const float e = __ldg(y + l) - fit(l);
+            acc0 = fmaf(e, e, acc0);
+        }
+        rms[n] = sqrtf((acc0 + acc1) / (float)L);
     }
-    rms[n] = sqrtf(acc / (float)L);
 }
 
 template <int NJ4>
@@ -579,8 +626,9 @@ static cudaError_t launch_rms_t(const float *cube, const float *S, const float *
     cudaError_t e = cudaFuncSetAttribute(rms_kernel<NJ4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long long blocks = (N + RMS_THREADS - 1) / RMS_THREADS;
-    rms_kernel<NJ4><<<(unsigned)blocks, RMS_THREADS, smem, st>>>(cube, S, x, N, L, P, rms);
+    const unsigned blocks = persistent_blocks(rms_kernel<NJ4>, RMS_THREADS, smem, N);
+    rms_kernel<NJ4><<<blocks, RMS_THREADS, smem, st>>>(cube, S, x, N, L, P, rms,
+                                                      rows_aligned(cube, L));
     return cudaGetLastError();
 }
 
