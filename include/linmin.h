@@ -85,7 +85,7 @@ enum { LINMIN_PROJ_DF = 0 };
 /* Constraint set.  LINMIN_STO: x >= 0 and sum x = 1 (Sec. 2.2, FCLS). */
 enum { LINMIN_STO = 0 };
 
-#define LINMIN_MAX_P 48
+#define LINMIN_MAX_P 64
 #define LINMIN_MAX_L 4096
 
 typedef struct {
@@ -107,7 +107,7 @@ enum {
     LINMIN_PHASE_PREP = 0,      /* whitening, fp64 Gram, splits (3 kernels) */
     LINMIN_PHASE_PROJECT = 1,   /* double-float projection c = S W^2 y */
     LINMIN_PHASE_IPM = 2,       /* interior point, float32 residual, all pixels */
-    LINMIN_PHASE_CROSSOVER = 3, /* fp64 active-set finish + uncertainties */
+    LINMIN_PHASE_CROSSOVER = 3, /* double-float active-set finish + uncertainties */
     LINMIN_PHASE_RETRY = 4,     /* pixels the crossover could not finish:
                                    interior point with the double-float
                                    residual, then the crossover again */
@@ -136,7 +136,7 @@ LINMIN_API linmin_status linmin_create(const float *library, int L, int P,
 /*
  * Unmix N pixels: whitening (Sec. 2.3), projection c = S W^2 y,
  * primal-dual interior-point FCLS per pixel (Sec. 2.2) until the support of
- * the solution is identified, an fp64 active-set crossover to the exact
+ * the solution is identified, a double-float active-set crossover to the exact
  * minimiser (the few pixels it cannot finish are re-solved with a
  * double-float KKT residual), abundance uncertainties (Sec. 2.3) and the RMS
  * of the fit.
@@ -170,6 +170,13 @@ LINMIN_API linmin_status linmin_destroy(linmin_handle h);
 /* One-line description of the last error on h (or of the last failed
  * linmin_create when h is NULL).  The string lives until the next call. */
 LINMIN_API const char *linmin_last_error(linmin_handle h);
+
+/* Number of kernel launches the last linmin_unmix on h queued (0 before the
+ * first call or for N = 0; -1 for a NULL handle).  A fixed pipeline: 3
+ * preparation kernels, the projection, the interior-point kernel, the
+ * crossover (support, counting sort, MAX_SWAPS + 1 passes), the retry path
+ * (two interior-point kernels, support, MAX_SWAPS + 1 passes) and the RMS. */
+LINMIN_API int linmin_last_launches(linmin_handle h);
 
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);

@@ -55,6 +55,7 @@ struct linmin_ctx {
     // phase events (profile mode)
     cudaEvent_t ev[LINMIN_NUM_PHASES + 1] = {};
     bool timed = false;
+    int launches = 0;            // kernel launches of the last linmin_unmix
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -263,6 +264,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
 {
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
     if (N < 0) return fail(h, LINMIN_ERR_INVALID, "N < 0");
+    h->launches = 0;
     if (N == 0) return LINMIN_OK;
     if (!cube || !sigma) return fail(h, LINMIN_ERR_INVALID, "cube or sigma is NULL");
     if (N > (1LL << 40)) return fail(h, LINMIN_ERR_INVALID, "N too large");
@@ -347,6 +349,8 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
     h->timed = h->opt.profile != 0;
+    h->launches = PREP_LAUNCHES + 1 + 1 + crossover_launches(true) + 2 + crossover_launches(false) +
+                  (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
                       "copy iterations");
 
@@ -410,6 +414,11 @@ linmin_status linmin_destroy(linmin_handle h)
         if (p) cudaFree(p);
     delete h;
     return LINMIN_OK;
+}
+
+int linmin_last_launches(linmin_handle h)
+{
+    return h ? h->launches : -1;
 }
 
 const char *linmin_last_error(linmin_handle h)

@@ -69,9 +69,11 @@ struct IpmCfg {
     static constexpr int NS = NS_, G = G_;
     static constexpr int PP = NS * G;      // padded size, multiple of 4
     static constexpr int GPW = 32 / G;     // pixel groups per warp
-    // resident blocks per SM the register budget is sized for: 9 slots of
-    // 4 lanes hold 180 registers of H per lane, so 2 blocks; others 3
-    static constexpr int MIN_BLOCKS = NS >= 8 ? 2 : 3;
+    // registers of H per lane (rows of (s+1)*G floats) and the resident
+    // blocks per SM the register budget is sized for: 2 blocks above 100
+    // registers of H (9x4: 180, 4x16: 160, 5x8: 120), else 3
+    static constexpr int H_REGS = NS * (NS + 1) / 2 * G;
+    static constexpr int MIN_BLOCKS = H_REGS > 100 ? 2 : 3;
     static constexpr int WARPS = 4;       // warps per block
     static constexpr int THREADS = WARPS * 32;
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)

@@ -38,5 +38,6 @@ LM_DECLARE_BUCKET(4, 8)
 LM_DECLARE_BUCKET(9, 4)
 LM_DECLARE_BUCKET(5, 8)
 LM_DECLARE_BUCKET(3, 16)
+LM_DECLARE_BUCKET(4, 16)
 
 }  // namespace lm

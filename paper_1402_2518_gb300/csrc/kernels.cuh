@@ -35,6 +35,11 @@ struct Prep {
     int *flags;      // 1       bit 0: invalid sigma, bit 1: bad scale
 };
 
+// kernel launches issued by launch_prep and launch_crossover (kept next to
+// them so that the launch count the C ABI reports stays exact)
+constexpr int PREP_LAUNCHES = 3;
+constexpr int crossover_launches(bool whole_cube) { return (whole_cube ? 3 : 1) + MAX_SWAPS + 1; }
+
 cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP,
                         const Prep &o, cudaStream_t st);
 cudaError_t launch_project(const float *cube, long long N, int L, int P,

@@ -23,7 +23,7 @@ LINMIN_ERR_NOT_CONVERGED = 6
 LINMIN_ERR_UNSUPPORTED = 7
 LINMIN_PROJ_DF = 0
 LINMIN_STO = 0
-LINMIN_MAX_P = 48
+LINMIN_MAX_P = 64
 LINMIN_MAX_L = 4096
 
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_RANK",
@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_
 
 EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_wait",
             "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version",
-            "linmin_unmix_noalloc")
+            "linmin_unmix_noalloc", "linmin_last_launches")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
 
@@ -81,6 +81,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_unmix_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_longlong,
                                          P, P, P, P, P, ctypes.c_void_p]
     lib.linmin_unmix_noalloc.restype = ctypes.c_int
+    lib.linmin_last_launches.argtypes = [H]
+    lib.linmin_last_launches.restype = ctypes.c_int
     lib.linmin_version.argtypes = []
     lib.linmin_version.restype = ctypes.c_char_p
     return lib
@@ -176,6 +178,11 @@ def linmin_unmix_noalloc(library, L: int, P: int, cube, N: int, sigma, abundance
     return lib().linmin_unmix_noalloc(_ptr(library), int(L), int(P), _ptr(cube), int(N),
                                       _ptr(sigma), _ptr(abundances), _ptr(uncertainties),
                                       _ptr(residual_rms), _ptr(iterations, "int32"), st)
+
+
+def linmin_last_launches(h) -> int:
+    """Kernel launches queued by the last linmin_unmix on h."""
+    return lib().linmin_last_launches(h)
 
 
 def linmin_version() -> str:

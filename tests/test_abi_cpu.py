@@ -65,8 +65,8 @@ def test_invalid_arguments_rejected_on_host():
     assert lib.linmin_create(None, 16, 4, None, ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
     assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, 0, None,
                              ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
-    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, 49, None,
-                             ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
+    assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 16, linmin.LINMIN_MAX_P + 1,
+                             None, ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
     assert lib.linmin_create(S.ctypes.data_as(ctypes.c_void_p), 3, 4, None,
                              ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
     # four identical spectra: rank [S^T; 1^T] = 1 < 4

@@ -120,6 +120,15 @@ def test_random_small_libraries(pkg, seed):
     check(gpu, ref, cube.S, cube.sigma, cube.X)
 
 
+@pytest.mark.parametrize("P", [49, 57, 64])
+def test_large_libraries(pkg, P):
+    """The P <= 64 size bucket (16 lanes per pixel, padded rows for P < 64)."""
+    cube = synth.random_instance(900 + P, 300, P + 40, P, n_extras=4, kmax=5)
+    ref = oracle.unmix(cube.S, cube.sigma, cube.X)
+    gpu = run_gpu(pkg, cube.S, cube.sigma, cube.X)
+    check(gpu, ref, cube.S, cube.sigma, cube.X)
+
+
 def test_P1_and_N1(pkg):
     rng = np.random.Generator(np.random.PCG64(7))
     S = rng.uniform(0.2, 0.6, (1, 20)).astype(np.float32)
