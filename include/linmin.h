@@ -159,9 +159,20 @@ LINMIN_API linmin_status linmin_wait(linmin_handle h, long long *n_not_converged
 
 /* Device time (ms) of each phase of the last linmin_unmix on h, measured
  * with CUDA events on the handle's stream; requires opt.profile.  ms_out
- * receives min(n, LINMIN_NUM_PHASES) values; synchronises the stream.
- * Returns LINMIN_ERR_INVALID when profiling is off or nothing ran yet. */
+ * receives min(n, LINMIN_NUM_PHASES) values; waits for that call's last
+ * event.  Returns LINMIN_ERR_INVALID when profiling is off or nothing ran
+ * yet. */
 LINMIN_API linmin_status linmin_phase_times(linmin_handle h, float *ms_out, int n);
+
+/* Number of past calls whose phase events a handle keeps. */
+#define LINMIN_PHASE_RING 32
+
+/* As linmin_phase_times for the call `back` calls before the last one
+ * (back = 0: the last call), 0 <= back < LINMIN_PHASE_RING: calls queued
+ * back to back can be timed phase by phase after one synchronisation.
+ * LINMIN_ERR_INVALID when that call is not (or no longer) recorded. */
+LINMIN_API linmin_status linmin_phase_times_at(linmin_handle h, int back, float *ms_out,
+                                               int n);
 
 /* Free the handle and its device memory (synchronises its stream first).
  * NULL is accepted. */

@@ -5,6 +5,6 @@ from ``csrc/``; ``linmin`` is its ctypes binding.
 """
 from .linmin import (EXPORTED, LinminError, Unmixer, library_path, linmin_create,  # noqa: F401
                      linmin_default_options, linmin_destroy, linmin_last_error,
-                     linmin_options, linmin_phase_times, linmin_unmix, linmin_unmix_noalloc,
+                     linmin_options, linmin_phase_times, linmin_phase_times_at, linmin_unmix, linmin_unmix_noalloc,
                      linmin_last_launches, linmin_version,
                      linmin_wait, load)

@@ -53,14 +53,17 @@ struct linmin_ctx {
           *io_rms = nullptr;
     int *io_it = nullptr;
     // phase events (profile mode)
-    cudaEvent_t ev[LINMIN_NUM_PHASES + 1] = {};
-    bool timed = false;
+    // phase events of the last LINMIN_PHASE_RING calls (ring of event sets),
+    // so that a caller can read the phase times of several queued calls
+    // after one synchronisation
+    cudaEvent_t ev[LINMIN_PHASE_RING][LINMIN_NUM_PHASES + 1] = {};
+    long long calls = 0;          // profiled calls so far (ring position)
     int launches = 0;            // kernel launches of the last linmin_unmix
 };
 
 static void mark(linmin_ctx *h, int i)
 {
-    if (h->opt.profile) cudaEventRecord(h->ev[i], h->stream);
+    if (h->opt.profile) cudaEventRecord(h->ev[h->calls % LINMIN_PHASE_RING][i], h->stream);
 }
 
 static std::string g_create_error;
@@ -206,7 +209,8 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     A(dalloc(&h->xw.hist, (size_t)P + 1));
     A(cudaMemcpy(h->dS, hS.data(), hS.size() * 4, cudaMemcpyHostToDevice));
     if (o.profile)
-        for (int i = 0; i <= LINMIN_NUM_PHASES; ++i) A(cudaEventCreate(&h->ev[i]));
+        for (auto &set : h->ev)
+            for (cudaEvent_t &e : set) A(cudaEventCreate(&e));
 #undef A
     if (a != cudaSuccess) {
         linmin_status st = cuda_fail(nullptr, a, "linmin_create allocation");
@@ -348,7 +352,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     mark(h, 5);
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
-    h->timed = h->opt.profile != 0;
+    if (h->opt.profile) ++h->calls;
     h->launches = PREP_LAUNCHES + 1 + 1 + crossover_launches(true) + 2 + crossover_launches(false) +
                   (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
@@ -386,13 +390,21 @@ linmin_status linmin_wait(linmin_handle h, long long *n_not_converged)
 
 linmin_status linmin_phase_times(linmin_handle h, float *ms_out, int n)
 {
+    return linmin_phase_times_at(h, 0, ms_out, n);
+}
+
+linmin_status linmin_phase_times_at(linmin_handle h, int back, float *ms_out, int n)
+{
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
-    if (!h->opt.profile || !h->timed || !ms_out)
-        return fail(h, LINMIN_ERR_INVALID, "profiling is off or nothing was timed");
-    LM_CUDA(h, cudaEventSynchronize(h->ev[LINMIN_NUM_PHASES]), "event sync");
+    if (!h->opt.profile || !ms_out)
+        return fail(h, LINMIN_ERR_INVALID, "profiling is off");
+    if (back < 0 || back >= LINMIN_PHASE_RING || back >= h->calls)
+        return fail(h, LINMIN_ERR_INVALID, "no such profiled call");
+    cudaEvent_t *set = h->ev[(h->calls - 1 - back) % LINMIN_PHASE_RING];
+    LM_CUDA(h, cudaEventSynchronize(set[LINMIN_NUM_PHASES]), "event sync");
     for (int i = 0; i < n && i < LINMIN_NUM_PHASES; ++i) {
         float ms = 0.f;
-        LM_CUDA(h, cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]), "event time");
+        LM_CUDA(h, cudaEventElapsedTime(&ms, set[i], set[i + 1]), "event time");
         ms_out[i] = ms;
     }
     return LINMIN_OK;
@@ -402,8 +414,9 @@ linmin_status linmin_destroy(linmin_handle h)
 {
     if (!h) return LINMIN_OK;
     cudaStreamSynchronize(h->stream);
-    for (cudaEvent_t e : h->ev)
-        if (e) cudaEventDestroy(e);
+    for (auto &set : h->ev)
+        for (cudaEvent_t e : set)
+            if (e) cudaEventDestroy(e);
     void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
                     h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
                     h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,

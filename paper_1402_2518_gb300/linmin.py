@@ -31,8 +31,9 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_
 
 EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_wait",
             "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version",
-            "linmin_unmix_noalloc", "linmin_last_launches")
+            "linmin_unmix_noalloc", "linmin_last_launches", "linmin_phase_times_at")
 LINMIN_NOALLOC_SCRATCH_MB = 64
+LINMIN_PHASE_RING = 32
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
 
 
@@ -81,6 +82,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_unmix_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_longlong,
                                          P, P, P, P, P, ctypes.c_void_p]
     lib.linmin_unmix_noalloc.restype = ctypes.c_int
+    lib.linmin_phase_times_at.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.c_int]
+    lib.linmin_phase_times_at.restype = ctypes.c_int
     lib.linmin_last_launches.argtypes = [H]
     lib.linmin_last_launches.restype = ctypes.c_int
     lib.linmin_version.argtypes = []
@@ -158,6 +162,13 @@ def linmin_phase_times(h) -> dict:
     """Per-phase device milliseconds of the last linmin_unmix (profile mode)."""
     arr = (ctypes.c_float * len(PHASES))()
     _check(lib().linmin_phase_times(h, arr, len(PHASES)), h)
+    return {k: float(v) for k, v in zip(PHASES, arr)}
+
+
+def linmin_phase_times_at(h, back: int) -> dict:
+    """Per-phase device milliseconds of the call `back` calls before the last."""
+    arr = (ctypes.c_float * len(PHASES))()
+    _check(lib().linmin_phase_times_at(h, back, arr, len(PHASES)), h)
     return {k: float(v) for k, v in zip(PHASES, arr)}
 
 

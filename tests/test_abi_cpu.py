@@ -44,7 +44,7 @@ def test_header_constants_match_binding():
                  "LINMIN_ERR_UNSUPPORTED"):
         m = re.search(rf"{name}\s*=\s*(\d+)", txt)
         assert m and int(m.group(1)) == getattr(linmin, name)
-    for name in ("LINMIN_MAX_P", "LINMIN_MAX_L", "LINMIN_NOALLOC_SCRATCH_MB"):
+    for name in ("LINMIN_MAX_P", "LINMIN_MAX_L", "LINMIN_NOALLOC_SCRATCH_MB", "LINMIN_PHASE_RING"):
         m = re.search(rf"#define {name} (\d+)", txt)
         assert m and int(m.group(1)) == getattr(linmin, name)
 
