@@ -66,6 +66,12 @@ def parse():
     ap.add_argument("--pixels", type=int, default=0,
                     help="use only the first PIXELS pixels (small profiling case)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serving-cubes", type=int, default=64)
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="arrivals per second")
+    ap.add_argument("--serving-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-chunk", type=int, default=65536)
     return ap.parse_args()
 
 
@@ -208,6 +214,93 @@ def run_reference(args, cube):
     print(json.dumps(line))
 
 
+def _pct(v, q):
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def run_serving(pkg, dev, n_cubes: int, rate: float, budget_gb: float, slots: int,
+                chunk: int):
+    """Serving stream of uneven cubes through the library's server (chunks of
+    all requests in flight on `slots` streams) against the plain path: one
+    linmin_unmix call per cube, one after the other.  Inputs and outputs are
+    device-resident; latency = completion - arrival (queueing included).
+    Also the same cubes all submitted at once (a batch)."""
+    import torch
+    specs = synth.batch_specs(n_cubes)
+    arrivals = synth.poisson_arrivals(n_cubes, rate)
+    cubes = []
+    for sp in specs:
+        c = synth.make_cube(sp)
+        cubes.append((torch.from_numpy(c.S).to(dev), torch.from_numpy(c.X).to(dev),
+                      torch.from_numpy(c.sigma).to(dev), c.N, c.P))
+    outs = [(torch.empty((N, P), device=dev), torch.empty((N, P), device=dev),
+             torch.empty((N,), device=dev), torch.empty((N,), dtype=torch.int32, device=dev))
+            for (_, _, _, N, P) in cubes]
+    total = sum(c[3] for c in cubes)
+
+    def served(arr):
+        srv = pkg.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), slots=slots,
+                         chunk_pixels=chunk)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = []
+        for (S, X, sg, N, P), o, ta in zip(cubes, outs, arr):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            t_call = time.perf_counter() - t0
+            tickets.append((srv.submit(S, X, sg, *o), t_call))
+        lat, end, bad = [], 0.0, 0
+        for (t, sub), ta in zip(tickets, arr):
+            st, ms = srv.wait(t)
+            bad += st != 0
+            lat.append(ms + (sub - ta) * 1e3)      # + the submit call's delay behind the arrival
+            end = max(end, ta + lat[-1] / 1e3)
+        stats = srv.stats()
+        srv.close()
+        return {"value": total / end, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "makespan_s": end, "failed": bad,
+                "max_running": stats["max_running"], "chunks": stats["chunks"],
+                "handles_created": stats["handles_created"],
+                "peak_gb": stats["peak_bytes"] / (1 << 30)}
+
+    def plain(arr):
+        hs = []
+        for (S, X, sg, N, P) in cubes:
+            um = pkg.Unmixer(S)
+            hs.append(um)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat, bad = [], 0
+        for um, (S, X, sg, N, P), o, ta in zip(hs, cubes, outs, arr):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            pkg.linmin_unmix(um.h, X, N, sg, *o)
+            st, _ = um.wait()
+            bad += st != 0
+            lat.append((time.perf_counter() - t0 - ta) * 1e3)
+        end = time.perf_counter() - t0
+        for um in hs:
+            um.close()
+        return {"value": total / end, "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99),
+                "makespan_s": end, "failed": bad}
+
+    # warm-up (first launches of each kernel size, allocator)
+    served(np.zeros(n_cubes))
+    res = {"workload": f"{n_cubes} cubes, N log-uniform 1e3..3e5, L in {{128,184,240}}, "
+                       f"P in {{16,32,48,64}} (P-4 minerals + 4 extras), Poisson {rate:g}/s",
+           "pixels": total, "unit": "pixels/s", "slots": slots, "chunk_pixels": chunk,
+           "hbm_budget_gb": budget_gb, "inputs": "device-resident"}
+    res["stream"] = served(arrivals)
+    res["stream_plain"] = plain(arrivals)
+    res["batch"] = served(np.zeros(n_cubes))
+    res["batch_plain"] = plain(np.zeros(n_cubes))
+    res["plain_note"] = ("one linmin_unmix per cube, sequential, handles created before "
+                         "the timed stream")
+    return res
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -287,6 +380,10 @@ def main():
         e2e = {"value": N * ws / e2e_s, "unit": "pixels/s",
                "h2d_bytes_per_step": N * L * 4 + L * 4,
                "d2h_bytes_per_step": N * (2 * P + 2) * 4}
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,
+                              args.serving_budget_gb, args.serving_slots, args.serving_chunk)
     if rank != 0:
         dist.barrier() if ws > 1 else None
         return
@@ -326,6 +423,7 @@ def main():
         "gpu_launches": launches * args.steps,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line))
     if ws > 1:

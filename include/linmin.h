@@ -192,6 +192,94 @@ LINMIN_API int linmin_last_launches(linmin_handle h);
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);
 
+/* ------------------------------------------------------------------ */
+/*
+ * Serving: continuous batching of unmixing requests.  The paper has no
+ * counterpart (it unmixes one cube at a time); this is the runtime that
+ * runs cubes of different sizes and libraries as they arrive.
+ *
+ * A request (one cube against one library) is cut into chunks of at most
+ * chunk_pixels pixels; `slots` worker threads, each with its own CUDA
+ * stream, run the chunks of all requests, oldest request first, so the
+ * chunks of different requests overlap on the device and a request that
+ * arrives while others run starts as soon as a slot and device memory are
+ * free.  Each worker keeps a handle (library copy, per-sigma factors,
+ * scratch reserved for one chunk) per library it served; the device bytes
+ * of all handles stay within hbm_budget_bytes (idle handles are destroyed,
+ * least recently used first, to make room; otherwise the chunk waits).
+ * Results are bit-identical to a linmin_unmix call over the whole cube.
+ */
+typedef struct linmin_server_s *linmin_server;
+
+typedef struct {
+    unsigned long long hbm_budget_bytes; /* device bytes of the server's handles
+                                            (default 1 GiB; allocation
+                                            granularity not counted) */
+    int slots;                /* worker streams = chunks in flight (1..64, default 4) */
+    long long chunk_pixels;   /* pixels per chunk (default 65536) */
+    int max_iter;             /* interior-point cap per pixel (default 100) */
+} linmin_server_options;
+
+/* One cube.  Pointers as in linmin_create / linmin_unmix (host or device;
+ * NULL outputs are skipped); every buffer must stay valid until
+ * linmin_server_wait returns for the request. */
+typedef struct {
+    const float *library;     /* P x L */
+    int L, P;
+    const float *cube;        /* N x L */
+    long long N;
+    const float *sigma;       /* L */
+    float *abundances;        /* N x P */
+    float *uncertainties;     /* N x P */
+    float *residual_rms;      /* N */
+    int *iterations;          /* N */
+} linmin_request;
+
+typedef struct {
+    unsigned long long requests, requests_done, chunks;
+    unsigned long long handles_created, evictions;
+    unsigned long long bytes, peak_bytes;  /* device bytes of handles: now / at most */
+    int running, max_running;              /* chunks on the device: now / at most */
+} linmin_server_stats;
+
+LINMIN_API linmin_status linmin_server_default_options(linmin_server_options *opt);
+
+/* Start the worker threads on the current device.  LINMIN_ERR_INVALID for
+ * out-of-range options, LINMIN_ERR_CUDA without a usable device. */
+LINMIN_API linmin_status linmin_server_create(const linmin_server_options *opt,
+                                              linmin_server *out);
+
+/* Queue a request; *ticket identifies it.  Checked before queueing (the
+ * same errors as linmin_create, LINMIN_ERR_OOM when one chunk's handle
+ * cannot fit the budget); a library is checked (and its rank computed) on
+ * every submit.  Thread-safe. */
+LINMIN_API linmin_status linmin_server_submit(linmin_server s, const linmin_request *req,
+                                              long long *ticket);
+
+/* *done = 1 once every chunk of the request has finished.  Thread-safe. */
+LINMIN_API linmin_status linmin_server_poll(linmin_server s, long long ticket, int *done);
+
+/* Block until the request has finished; returns its status (the worst of
+ * its chunks: LINMIN_ERR_NOT_CONVERGED when some pixel hit max_iter) and,
+ * in *latency_ms (may be NULL), the time from submit to completion.  The
+ * ticket is released: wait once per ticket.  Thread-safe. */
+LINMIN_API linmin_status linmin_server_wait(linmin_server s, long long ticket,
+                                            double *latency_ms);
+
+LINMIN_API linmin_status linmin_server_get_stats(linmin_server s, linmin_server_stats *st);
+
+/* Device bytes one server handle holds for a library of L bands and P
+ * spectra with scratch for chunk_pixels pixels (host_io != 0: with the
+ * staging buffers of host-pointer requests); 0 when P is unsupported. */
+LINMIN_API unsigned long long linmin_server_handle_bytes(int L, int P, long long chunk_pixels,
+                                                         int host_io);
+
+/* Reason of the last failed submit/wait on s. */
+LINMIN_API const char *linmin_server_last_error(linmin_server s);
+
+/* Finish the queued requests, stop the workers, free every handle. */
+LINMIN_API linmin_status linmin_server_destroy(linmin_server s);
+
 /* Size in MiB of the static device scratch array of linmin_unmix_noalloc. */
 #define LINMIN_NOALLOC_SCRATCH_MB 64
 

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "api_internal.h"
 #include "ipm.cuh"
 #include "kernels.cuh"
 #include "linmin.h"
@@ -136,6 +137,46 @@ static bool full_rank(const std::vector<float> &S, int L, int P)
     return true;
 }
 
+namespace lm {
+
+linmin_status load_library(const float *library, int L, int P, std::vector<float> *host,
+                           std::string *why)
+{
+    host->assign((size_t)P * L, 0.f);
+    const bool on_dev = is_device_ptr(library);
+    if (on_dev) {
+        cudaError_t e = cudaMemcpy(host->data(), library, host->size() * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            *why = std::string("copy library: ") + cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? LINMIN_ERR_OOM : LINMIN_ERR_CUDA;
+        }
+    } else {
+        std::memcpy(host->data(), library, host->size() * 4);
+    }
+    for (float v : *host)
+        if (!std::isfinite(v)) { *why = "library has NaN/Inf"; return LINMIN_ERR_INVALID; }
+    if (!full_rank(*host, L, P)) {
+        *why = "rank [S^T; 1^T] < P: the constrained minimiser is not unique";
+        return LINMIN_ERR_RANK;
+    }
+    return LINMIN_OK;
+}
+
+size_t handle_bytes(int L, int P, long long N, bool host_io)
+{
+    Bucket b{};
+    if (!ipm_bucket(P, &b)) return 0;
+    const size_t PP = b.PP, PQ = pq_of(P), n = (size_t)(N > 0 ? N : 1);
+    size_t fixed = 4 * (size_t)P * L + 8 * 2 * (size_t)P * P + 8 + 4 * 2 * PP * PP + 4 * PP +
+                   4 * (size_t)P + 4 * 2 * (size_t)L * PQ + 4 + 8 * 8 +
+                   8 * (MAX_SWAPS + 2) + 8 + 8 * ((size_t)P + 1) + 4 * ((size_t)P + 1);
+    size_t per_pixel = 4 * 4 * (size_t)P + 4 + 4 + 8 + 8 + 8 + 8 + 4;
+    if (host_io) per_pixel += 4 * (size_t)L + 2 * 4 * (size_t)P + 4 + 4;
+    return fixed + (host_io ? 4 * (size_t)L : 0) + per_pixel * n;
+}
+
+}  // namespace lm
+
 extern "C" {
 
 const char *linmin_version(void) { return "linmin-gb300 0.1 (sm_103a)"; }
@@ -171,17 +212,10 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     if (o.max_iter < 1 || !(o.tol > 0.f) || !(o.refine_mu > 0.f))
         return fail(nullptr, LINMIN_ERR_INVALID, "max_iter >= 1, tol > 0, refine_mu > 0");
 
-    std::vector<float> hS((size_t)P * L);
-    const bool on_dev = is_device_ptr(library);
-    cudaError_t e = on_dev ? cudaMemcpy(hS.data(), library, hS.size() * 4, cudaMemcpyDeviceToHost)
-                           : cudaSuccess;
-    if (e != cudaSuccess) return cuda_fail(nullptr, e, "copy library");
-    if (!on_dev) std::memcpy(hS.data(), library, hS.size() * 4);
-    for (float v : hS)
-        if (!std::isfinite(v)) return fail(nullptr, LINMIN_ERR_INVALID, "library has NaN/Inf");
-    if (!full_rank(hS, L, P))
-        return fail(nullptr, LINMIN_ERR_RANK,
-                    "rank [S^T; 1^T] < P: the constrained minimiser is not unique");
+    std::vector<float> hS;
+    std::string why;
+    const linmin_status lst = lm::load_library(library, L, P, &hS, &why);
+    if (lst != LINMIN_OK) return fail(nullptr, lst, why);
 
     linmin_ctx *h = new linmin_ctx();
     h->L = L; h->P = P; h->opt = o;
@@ -441,3 +475,11 @@ const char *linmin_last_error(linmin_handle h)
 }
 
 }  // extern "C"
+
+// outside the C block: a C++ function of namespace lm
+linmin_status lm::reserve(linmin_handle h, long long N, bool host_io)
+{
+    linmin_status st = ensure_scratch(h, N);
+    if (st == LINMIN_OK && host_io) st = ensure_io(h, N);
+    return st;
+}

@@ -1,0 +1,24 @@
+// Internal entry points shared by the C ABI translation units (not exported).
+#pragma once
+#include <string>
+#include <vector>
+
+#include "linmin.h"
+
+namespace lm {
+
+// Copy a P x L library (host or device pointer) to *host and check it:
+// finite values and rank [S^T; 1^T] = P.  *why receives the reason of a
+// failure.
+linmin_status load_library(const float *library, int L, int P, std::vector<float> *host,
+                           std::string *why);
+
+// Device bytes a handle for (L, P) holds once reserved for N pixels (with
+// the host-pointer staging buffers when host_io).
+size_t handle_bytes(int L, int P, long long N, bool host_io);
+
+// Allocate a handle's per-pixel scratch (and staging) for N pixels now, so
+// that later calls with at most N pixels allocate nothing.
+linmin_status reserve(linmin_handle h, long long N, bool host_io);
+
+}  // namespace lm

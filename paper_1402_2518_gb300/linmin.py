@@ -31,7 +31,10 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_
 
 EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_wait",
             "linmin_phase_times", "linmin_destroy", "linmin_last_error", "linmin_version",
-            "linmin_unmix_noalloc", "linmin_last_launches", "linmin_phase_times_at")
+            "linmin_unmix_noalloc", "linmin_last_launches", "linmin_phase_times_at",
+            "linmin_server_default_options", "linmin_server_create", "linmin_server_submit",
+            "linmin_server_poll", "linmin_server_wait", "linmin_server_get_stats",
+            "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
@@ -42,6 +45,25 @@ class linmin_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("tol", ctypes.c_float),
                 ("refine_mu", ctypes.c_float), ("cuda_stream", ctypes.c_void_p),
                 ("profile", ctypes.c_int)]
+
+
+class linmin_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_ulonglong), ("slots", ctypes.c_int),
+                ("chunk_pixels", ctypes.c_longlong), ("max_iter", ctypes.c_int)]
+
+
+class linmin_request(ctypes.Structure):
+    _fields_ = [("library", ctypes.c_void_p), ("L", ctypes.c_int), ("P", ctypes.c_int),
+                ("cube", ctypes.c_void_p), ("N", ctypes.c_longlong), ("sigma", ctypes.c_void_p),
+                ("abundances", ctypes.c_void_p), ("uncertainties", ctypes.c_void_p),
+                ("residual_rms", ctypes.c_void_p), ("iterations", ctypes.c_void_p)]
+
+
+class linmin_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_ulonglong) for n in
+                ("requests", "requests_done", "chunks", "handles_created", "evictions",
+                 "bytes", "peak_bytes")] + [("running", ctypes.c_int),
+                                            ("max_running", ctypes.c_int)]
 
 
 class LinminError(RuntimeError):
@@ -82,6 +104,28 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_unmix_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_longlong,
                                          P, P, P, P, P, ctypes.c_void_p]
     lib.linmin_unmix_noalloc.restype = ctypes.c_int
+    SV = ctypes.c_void_p
+    lib.linmin_server_default_options.argtypes = [ctypes.POINTER(linmin_server_options)]
+    lib.linmin_server_default_options.restype = ctypes.c_int
+    lib.linmin_server_create.argtypes = [ctypes.POINTER(linmin_server_options),
+                                         ctypes.POINTER(SV)]
+    lib.linmin_server_create.restype = ctypes.c_int
+    lib.linmin_server_submit.argtypes = [SV, ctypes.POINTER(linmin_request),
+                                         ctypes.POINTER(ctypes.c_longlong)]
+    lib.linmin_server_submit.restype = ctypes.c_int
+    lib.linmin_server_poll.argtypes = [SV, ctypes.c_longlong, ctypes.POINTER(ctypes.c_int)]
+    lib.linmin_server_poll.restype = ctypes.c_int
+    lib.linmin_server_wait.argtypes = [SV, ctypes.c_longlong, ctypes.POINTER(ctypes.c_double)]
+    lib.linmin_server_wait.restype = ctypes.c_int
+    lib.linmin_server_get_stats.argtypes = [SV, ctypes.POINTER(linmin_server_stats)]
+    lib.linmin_server_get_stats.restype = ctypes.c_int
+    lib.linmin_server_last_error.argtypes = [SV]
+    lib.linmin_server_last_error.restype = ctypes.c_char_p
+    lib.linmin_server_handle_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                               ctypes.c_int]
+    lib.linmin_server_handle_bytes.restype = ctypes.c_ulonglong
+    lib.linmin_server_destroy.argtypes = [SV]
+    lib.linmin_server_destroy.restype = ctypes.c_int
     lib.linmin_phase_times_at.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.c_int]
     lib.linmin_phase_times_at.restype = ctypes.c_int
@@ -238,6 +282,120 @@ class Unmixer:
         if self.h:
             linmin_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+def linmin_server_default_options() -> linmin_server_options:
+    o = linmin_server_options()
+    _check(lib().linmin_server_default_options(ctypes.byref(o)))
+    return o
+
+
+def linmin_server_create(opt: linmin_server_options | None = None):
+    s = ctypes.c_void_p()
+    st = lib().linmin_server_create(ctypes.byref(opt) if opt is not None else None,
+                                    ctypes.byref(s))
+    if st != LINMIN_OK:
+        raise LinminError(st, "linmin_server_create failed")
+    return s
+
+
+def linmin_server_submit(s, library, L: int, P: int, cube, N: int, sigma, abundances=None,
+                         uncertainties=None, residual_rms=None, iterations=None) -> int:
+    """Queue one cube; returns its ticket (raises on a rejected request)."""
+    r = linmin_request(_ptr(library), int(L), int(P), _ptr(cube), int(N), _ptr(sigma),
+                       _ptr(abundances), _ptr(uncertainties), _ptr(residual_rms),
+                       _ptr(iterations, "int32"))
+    t = ctypes.c_longlong(0)
+    st = lib().linmin_server_submit(s, ctypes.byref(r), ctypes.byref(t))
+    if st != LINMIN_OK:
+        raise LinminError(st, linmin_server_last_error(s))
+    return t.value
+
+
+def linmin_server_poll(s, ticket: int) -> bool:
+    d = ctypes.c_int(0)
+    _check(lib().linmin_server_poll(s, int(ticket), ctypes.byref(d)))
+    return bool(d.value)
+
+
+def linmin_server_wait(s, ticket: int) -> tuple[int, float]:
+    """(status, latency in ms from submit to completion) of a request."""
+    ms = ctypes.c_double(0.0)
+    st = lib().linmin_server_wait(s, int(ticket), ctypes.byref(ms))
+    return st, ms.value
+
+
+def linmin_server_get_stats(s) -> dict:
+    st = linmin_server_stats()
+    _check(lib().linmin_server_get_stats(s, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in linmin_server_stats._fields_}
+
+
+def linmin_server_last_error(s) -> str:
+    m = lib().linmin_server_last_error(s)
+    return m.decode() if m else ""
+
+
+def linmin_server_handle_bytes(L: int, P: int, chunk_pixels: int, host_io: bool = False) -> int:
+    """Device bytes of one server handle (library + scratch for a chunk)."""
+    return lib().linmin_server_handle_bytes(int(L), int(P), int(chunk_pixels), int(host_io))
+
+
+def linmin_server_destroy(s) -> int:
+    return lib().linmin_server_destroy(s)
+
+
+class Server:
+    """Owner of a linmin server; keeps every request's arrays alive until
+    its ticket is waited on (the C side reads and writes them meanwhile)."""
+
+    def __init__(self, hbm_budget_bytes: int | None = None, slots: int | None = None,
+                 chunk_pixels: int | None = None, max_iter: int | None = None):
+        o = linmin_server_default_options()
+        if hbm_budget_bytes is not None:
+            o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if slots is not None:
+            o.slots = int(slots)
+        if chunk_pixels is not None:
+            o.chunk_pixels = int(chunk_pixels)
+        if max_iter is not None:
+            o.max_iter = int(max_iter)
+        self.s = linmin_server_create(o)
+        self._keep = {}
+
+    def submit(self, library, cube, sigma, abundances=None, uncertainties=None,
+               residual_rms=None, iterations=None) -> int:
+        P, L = library.shape
+        N = cube.shape[0]
+        t = linmin_server_submit(self.s, library, L, P, cube, N, sigma, abundances,
+                                 uncertainties, residual_rms, iterations)
+        self._keep[t] = (library, cube, sigma, abundances, uncertainties, residual_rms,
+                         iterations)
+        return t
+
+    def poll(self, ticket: int) -> bool:
+        return linmin_server_poll(self.s, ticket)
+
+    def wait(self, ticket: int) -> tuple[int, float]:
+        st, ms = linmin_server_wait(self.s, ticket)
+        self._keep.pop(ticket, None)
+        return st, ms
+
+    def stats(self) -> dict:
+        return linmin_server_get_stats(self.s)
+
+    def close(self):
+        if self.s:
+            linmin_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -89,3 +89,58 @@ def test_binding_rejects_wrong_dtypes():
         pkg.linmin_create(np.ones((4, 16)), 16, 4)          # float64
     with pytest.raises(ValueError):
         pkg.linmin_create(np.ones((16, 4), np.float32).T, 16, 4)  # not contiguous
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof/offsetof of every ABI struct, compiled from the header by the
+    host C compiler, equal the ctypes layouts of the binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"linmin_options": linmin.linmin_options,
+               "linmin_server_options": linmin.linmin_server_options,
+               "linmin_request": linmin.linmin_request,
+               "linmin_server_stats": linmin.linmin_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "linmin.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append('return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(out[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_server_options_defaults_and_invalid():
+    o = pkg.linmin_server_default_options()
+    assert o.hbm_budget_bytes == 1 << 30 and o.slots == 4 and o.chunk_pixels == 65536
+    assert o.max_iter == 100
+    lib = pkg.load()
+    bad = pkg.linmin_server_default_options()
+    bad.slots = 0
+    s = ctypes.c_void_p()
+    assert lib.linmin_server_create(ctypes.byref(bad), ctypes.byref(s)) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_server_create(None, None) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_server_submit(None, None, None) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_server_destroy(None) == linmin.LINMIN_OK
+
+
+def test_server_handle_bytes():
+    b = pkg.linmin_server_handle_bytes(184, 36, 1000)
+    b2 = pkg.linmin_server_handle_bytes(184, 36, 2000)
+    bh = pkg.linmin_server_handle_bytes(184, 36, 1000, host_io=True)
+    # per pixel: c~ hi/lo, x, lambda (4 P floats) + nu, iterations, retry,
+    # mask, two lists, support size (44 bytes); staging adds cube + outputs
+    assert b2 - b == 1000 * (16 * 36 + 44)
+    assert bh - b == 1000 * (4 * 184 + 8 * 36 + 8) + 4 * 184
+    assert pkg.linmin_server_handle_bytes(184, 65, 10) == 0
