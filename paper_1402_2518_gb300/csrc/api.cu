@@ -15,8 +15,11 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -60,6 +63,7 @@ struct linmin_ctx {
     cudaEvent_t ev[LINMIN_PHASE_RING][LINMIN_NUM_PHASES + 1] = {};
     long long calls = 0;          // profiled calls so far (ring position)
     int launches = 0;            // kernel launches of the last linmin_unmix
+    cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -98,12 +102,50 @@ static bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-template <typename T>
-static cudaError_t dalloc(T **p, size_t n)
+// Device memory of handles comes from a library-owned stream-ordered pool
+// per device whose freed blocks are kept for reuse while any handle lives:
+// creating and destroying handles (a serving loop does both) then neither
+// calls cudaMalloc/cudaFree nor synchronises the device.  The pool is
+// trimmed when the last handle of its device is destroyed.
+struct PoolState {
+    cudaMemPool_t pool = nullptr;
+    long long live = 0;              // handles of this device
+};
+static std::mutex g_pool_mu;
+static std::map<int, PoolState> g_pools;
+
+static cudaError_t pool_acquire(int dev, cudaMemPool_t *out)
 {
-    if (*p) { cudaFree(*p); *p = nullptr; }
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    PoolState &ps = g_pools[dev];
+    if (!ps.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaError_t e = cudaMemPoolCreate(&ps.pool, &props);
+        if (e != cudaSuccess) { ps.pool = nullptr; return e; }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(ps.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    ++ps.live;
+    *out = ps.pool;
+    return cudaSuccess;
+}
+
+static void pool_release(int dev)
+{
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    PoolState &ps = g_pools[dev];
+    if (--ps.live == 0 && ps.pool) cudaMemPoolTrimTo(ps.pool, 0);
+}
+
+template <typename T>
+static cudaError_t dalloc(linmin_ctx *h, T **p, size_t n)
+{
+    if (*p) { cudaFreeAsync(*p, h->stream); *p = nullptr; }
     if (n == 0) n = 1;
-    return cudaMalloc((void **)p, n * sizeof(T));
+    return cudaMallocFromPoolAsync((void **)p, n * sizeof(T), h->pool, h->stream);
 }
 
 // rank [S^T; 1^T] == P in fp64 (modified Gram-Schmidt with one
@@ -216,43 +258,7 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     std::string why;
     const linmin_status lst = lm::load_library(library, L, P, &hS, &why);
     if (lst != LINMIN_OK) return fail(nullptr, lst, why);
-
-    linmin_ctx *h = new linmin_ctx();
-    h->L = L; h->P = P; h->opt = o;
-    h->stream = (cudaStream_t)o.cuda_stream;
-    cudaGetDevice(&h->device);
-    if (!ipm_bucket(P, &h->bucket)) { delete h; return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P"); }
-    const int PP = h->bucket.PP, PQ = pq_of(P);
-    cudaError_t a = cudaSuccess;
-#define A(call) if (a == cudaSuccess) a = (call)
-    A(dalloc(&h->dS, (size_t)P * L));
-    A(dalloc(&h->prep.G64, (size_t)P * P));
-    A(dalloc(&h->prep.Gt64, (size_t)P * P));
-    A(dalloc(&h->prep.scale, 1));
-    A(dalloc(&h->prep.Ghi, (size_t)PP * PP));
-    A(dalloc(&h->prep.Glo, (size_t)PP * PP));
-    A(dalloc(&h->prep.grs, (size_t)PP));
-    A(dalloc(&h->prep.gdiag, (size_t)P));
-    A(dalloc(&h->prep.Bhi, (size_t)L * PQ));
-    A(dalloc(&h->prep.Blo, (size_t)L * PQ));
-    A(dalloc(&h->prep.flags, 1));
-    A(dalloc(&h->dcnt, 8));
-    A(dalloc(&h->xw.len, (size_t)MAX_SWAPS + 2));
-    A(dalloc(&h->xw.len_all, 1));
-    A(dalloc(&h->xw.cursor, (size_t)P + 1));
-    A(dalloc(&h->xw.hist, (size_t)P + 1));
-    A(cudaMemcpy(h->dS, hS.data(), hS.size() * 4, cudaMemcpyHostToDevice));
-    if (o.profile)
-        for (auto &set : h->ev)
-            for (cudaEvent_t &e : set) A(cudaEventCreate(&e));
-#undef A
-    if (a != cudaSuccess) {
-        linmin_status st = cuda_fail(nullptr, a, "linmin_create allocation");
-        linmin_destroy(h);
-        return st;
-    }
-    *out = h;
-    return LINMIN_OK;
+    return lm::create_from_host(hS.data(), L, P, o, out);
 }
 
 static linmin_status ensure_scratch(linmin_ctx *h, long long N)
@@ -261,17 +267,17 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     const size_t np = (size_t)N * h->P;
     cudaError_t a = cudaSuccess;
 #define A(call) if (a == cudaSuccess) a = (call)
-    A(dalloc(&h->c_hi, np));
-    A(dalloc(&h->c_lo, np));
-    A(dalloc(&h->x, np));
-    A(dalloc(&h->lam, np));
-    A(dalloc(&h->nu, (size_t)N));
-    A(dalloc(&h->it, (size_t)N));
-    A(dalloc(&h->retry, (size_t)N));
-    A(dalloc(&h->mask, (size_t)N));
-    A(dalloc(&h->xw.list[0], (size_t)N));
-    A(dalloc(&h->xw.list[1], (size_t)N));
-    A(dalloc(&h->xw.ksize, (size_t)N));
+    A(dalloc(h, &h->c_hi, np));
+    A(dalloc(h, &h->c_lo, np));
+    A(dalloc(h, &h->x, np));
+    A(dalloc(h, &h->lam, np));
+    A(dalloc(h, &h->nu, (size_t)N));
+    A(dalloc(h, &h->it, (size_t)N));
+    A(dalloc(h, &h->retry, (size_t)N));
+    A(dalloc(h, &h->mask, (size_t)N));
+    A(dalloc(h, &h->xw.list[0], (size_t)N));
+    A(dalloc(h, &h->xw.list[1], (size_t)N));
+    A(dalloc(h, &h->xw.ksize, (size_t)N));
 #undef A
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
@@ -284,12 +290,12 @@ static linmin_status ensure_io(linmin_ctx *h, long long N)
     const size_t np = (size_t)N * h->P;
     cudaError_t a = cudaSuccess;
 #define A(call) if (a == cudaSuccess) a = (call)
-    A(dalloc(&h->io_cube, (size_t)N * h->L));
-    A(dalloc(&h->io_sigma, (size_t)h->L));
-    A(dalloc(&h->io_x, np));
-    A(dalloc(&h->io_sx, np));
-    A(dalloc(&h->io_rms, (size_t)N));
-    A(dalloc(&h->io_it, (size_t)N));
+    A(dalloc(h, &h->io_cube, (size_t)N * h->L));
+    A(dalloc(h, &h->io_sigma, (size_t)h->L));
+    A(dalloc(h, &h->io_x, np));
+    A(dalloc(h, &h->io_sx, np));
+    A(dalloc(h, &h->io_rms, (size_t)N));
+    A(dalloc(h, &h->io_it, (size_t)N));
 #undef A
     if (a != cudaSuccess) { h->capIO = 0; return cuda_fail(h, a, "staging allocation"); }
     h->capIO = N;
@@ -448,20 +454,9 @@ linmin_status linmin_destroy(linmin_handle h)
 {
     if (!h) return LINMIN_OK;
     cudaStreamSynchronize(h->stream);
-    for (auto &set : h->ev)
-        for (cudaEvent_t e : set)
-            if (e) cudaEventDestroy(e);
-    void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
-                    h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
-                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
-                    h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
-                    h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
-                    h->io_x, h->io_sx, h->io_rms, h->io_it};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    delete h;
-    return LINMIN_OK;
+    return lm::destroy_async(h);
 }
+
 
 int linmin_last_launches(linmin_handle h)
 {
@@ -482,4 +477,74 @@ linmin_status lm::reserve(linmin_handle h, long long N, bool host_io)
     linmin_status st = ensure_scratch(h, N);
     if (st == LINMIN_OK && host_io) st = ensure_io(h, N);
     return st;
+}
+
+// A handle for a library already loaded and checked (lm::load_library),
+// with validated options.
+linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_options &o,
+                                   linmin_handle *out)
+{
+    *out = nullptr;
+    linmin_ctx *h = new linmin_ctx();
+    h->L = L; h->P = P; h->opt = o;
+    h->stream = (cudaStream_t)o.cuda_stream;
+    cudaGetDevice(&h->device);
+    if (!ipm_bucket(P, &h->bucket)) { delete h; return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P"); }
+    cudaError_t a = pool_acquire(h->device, &h->pool);
+    if (a != cudaSuccess) {
+        delete h;
+        return cuda_fail(nullptr, a, "memory pool");
+    }
+    const int PP = h->bucket.PP, PQ = pq_of(P);
+#define A(call) if (a == cudaSuccess) a = (call)
+    A(dalloc(h, &h->dS, (size_t)P * L));
+    A(dalloc(h, &h->prep.G64, (size_t)P * P));
+    A(dalloc(h, &h->prep.Gt64, (size_t)P * P));
+    A(dalloc(h, &h->prep.scale, 1));
+    A(dalloc(h, &h->prep.Ghi, (size_t)PP * PP));
+    A(dalloc(h, &h->prep.Glo, (size_t)PP * PP));
+    A(dalloc(h, &h->prep.grs, (size_t)PP));
+    A(dalloc(h, &h->prep.gdiag, (size_t)P));
+    A(dalloc(h, &h->prep.Bhi, (size_t)L * PQ));
+    A(dalloc(h, &h->prep.Blo, (size_t)L * PQ));
+    A(dalloc(h, &h->prep.flags, 1));
+    A(dalloc(h, &h->dcnt, 8));
+    A(dalloc(h, &h->xw.len, (size_t)MAX_SWAPS + 2));
+    A(dalloc(h, &h->xw.len_all, 1));
+    A(dalloc(h, &h->xw.cursor, (size_t)P + 1));
+    A(dalloc(h, &h->xw.hist, (size_t)P + 1));
+    A(cudaMemcpyAsync(h->dS, hS, (size_t)P * L * 4, cudaMemcpyHostToDevice, h->stream));
+    A(cudaStreamSynchronize(h->stream));       // hS belongs to the caller
+    if (o.profile)
+        for (auto &set : h->ev)
+            for (cudaEvent_t &e : set) A(cudaEventCreate(&e));
+#undef A
+    if (a != cudaSuccess) {
+        linmin_status st = cuda_fail(nullptr, a, "linmin_create allocation");
+        linmin_destroy(h);
+        return st;
+    }
+    *out = h;
+    return LINMIN_OK;
+}
+
+// Free a handle without waiting for its stream: every free is ordered
+// after the work already queued there.
+linmin_status lm::destroy_async(linmin_handle h)
+{
+    if (!h) return LINMIN_OK;
+    for (auto &set : h->ev)
+        for (cudaEvent_t e : set)
+            if (e) cudaEventDestroy(e);
+    void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
+                    h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
+                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
+                    h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
+                    h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
+                    h->io_x, h->io_sx, h->io_rms, h->io_it};
+    for (void *p : ptrs)
+        if (p) cudaFreeAsync(p, h->stream);
+    if (h->pool) pool_release(h->device);
+    delete h;
+    return LINMIN_OK;
 }

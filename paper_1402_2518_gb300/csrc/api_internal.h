@@ -13,6 +13,15 @@ namespace lm {
 linmin_status load_library(const float *library, int L, int P, std::vector<float> *host,
                            std::string *why);
 
+// A handle for a library already loaded and checked by load_library, with
+// validated options (no checks of its own).
+linmin_status create_from_host(const float *host_library, int L, int P,
+                               const linmin_options &opt, linmin_handle *out);
+
+// Free a handle without synchronising: its device memory returns to the
+// pool once the work already queued on its stream has run.
+linmin_status destroy_async(linmin_handle h);
+
 // Device bytes a handle for (L, P) holds once reserved for N pixels (with
 // the host-pointer staging buffers when host_io).
 size_t handle_bytes(int L, int P, long long N, bool host_io);

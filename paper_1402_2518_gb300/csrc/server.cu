@@ -135,7 +135,7 @@ bool make_room(linmin_server_s *s, size_t need)
         wv->handles.erase(kv);
         s->bytes -= e.bytes;
         ++s->st.evictions;
-        linmin_destroy(e.h);   // waits for that worker's stream; it holds no chunk of this handle
+        lm::destroy_async(e.h);   // ordered after that worker's queued work: no wait
     }
     return true;
 }
@@ -189,7 +189,8 @@ bool take_chunk(Worker *w, std::shared_ptr<Request> *req, long long *first, long
             o.max_iter = s->opt.max_iter;
             o.cuda_stream = w->stream;
             Entry e;
-            linmin_status st = linmin_create(rq->lib->host.data(), rq->r.L, rq->r.P, &o, &e.h);
+            linmin_status st = lm::create_from_host(rq->lib->host.data(), rq->r.L, rq->r.P, o,
+                                                    &e.h);
             if (st != LINMIN_OK) rq->err = linmin_last_error(nullptr);
             if (st == LINMIN_OK && (st = lm::reserve(e.h, rq->chunk, rq->host_io)) != LINMIN_OK)
                 rq->err = linmin_last_error(e.h);
