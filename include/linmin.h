@@ -189,6 +189,27 @@ LINMIN_API const char *linmin_last_error(linmin_handle h);
  * (two interior-point kernels, support, MAX_SWAPS + 1 passes) and the RMS. */
 LINMIN_API int linmin_last_launches(linmin_handle h);
 
+/* Lanes per pixel (G) of the interior-point kernel the handle runs: a
+ * pixel's H is spread over G lanes, NS = ceil(P / G) rows per lane
+ * (-1 for a NULL handle).  The default per P is the fastest measured on
+ * GB300 (4 lanes wherever the registers of H allow it). */
+LINMIN_API int linmin_get_lanes(linmin_handle h);
+
+/* Use G lanes per pixel from now on (a compiled bucket with P <= NS*G <
+ * P + 16 must exist, else LINMIN_ERR_UNSUPPORTED; the handle keeps its
+ * previous choice).  Results stay within the same tolerances. */
+LINMIN_API linmin_status linmin_set_lanes(linmin_handle h, int lanes);
+
+/* Autotuner: time the interior-point kernel of every compiled bucket that
+ * fits P (P <= NS*G < P + 16) on the first min(N, 32768) pixels of cube
+ * (host or device; sigma likewise), best of two runs each, and keep the
+ * fastest for the handle.  *lanes_out (may be NULL) receives its G,
+ * ms_out[i] (may be NULL; n_ms entries) the time of candidate i,
+ * *n_candidates (may be NULL) the number of candidates.  Synchronous. */
+LINMIN_API linmin_status linmin_autotune(linmin_handle h, const float *cube, long long N,
+                                         const float *sigma, int *lanes_out, float *ms_out,
+                                         int n_ms, int *n_candidates);
+
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);
 

@@ -209,7 +209,9 @@ size_t handle_bytes(int L, int P, long long N, bool host_io)
     Bucket b{};
     if (!ipm_bucket(P, &b)) return 0;
     const size_t PP = b.PP, PQ = pq_of(P), n = (size_t)(N > 0 ? N : 1);
-    size_t fixed = 4 * (size_t)P * L + 8 * 2 * (size_t)P * P + 8 + 4 * 2 * PP * PP + 4 * PP +
+    (void)b;
+    const size_t PPM = PP_MAX;
+    size_t fixed = 4 * (size_t)P * L + 8 * 2 * (size_t)P * P + 8 + 4 * 2 * PPM * PPM + 4 * PPM +
                    4 * (size_t)P + 4 * 2 * (size_t)L * PQ + 4 + 8 * 8 +
                    8 * (MAX_SWAPS + 2) + 8 + 8 * ((size_t)P + 1) + 4 * ((size_t)P + 1);
     size_t per_pixel = 4 * 4 * (size_t)P + 4 + 4 + 8 + 8 + 8 + 8 + 4;
@@ -282,6 +284,20 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
     return LINMIN_OK;
+}
+
+static IpmArgs ipm_args(linmin_ctx *h, long long N)
+{
+    IpmArgs ia;
+    ia.N = N; ia.P = h->P; ia.max_iter = h->opt.max_iter;
+    ia.c_hi = h->c_hi; ia.c_lo = h->c_lo;
+    ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
+    ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
+    ia.n_notconv = h->dcnt + 2;
+    ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    ia.list = nullptr; ia.list_len = nullptr;
+    ia.mu_ref = MU_STOP; ia.counter = h->dcnt + 0;
+    return ia;
 }
 
 static linmin_status ensure_io(linmin_ctx *h, long long N)
@@ -358,14 +374,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
             "projection kernel");
     mark(h, 2);
 
-    IpmArgs ia;
-    ia.N = N; ia.P = P; ia.max_iter = h->opt.max_iter;
-    ia.c_hi = h->c_hi; ia.c_lo = h->c_lo;
-    ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
-    ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
-    ia.n_notconv = h->dcnt + 2;
-    ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
-    ia.list = nullptr; ia.list_len = nullptr;
+    IpmArgs ia = ipm_args(h, N);
     // 3. all pixels: float32 residual until mu <= mu_stop
     ia.mu_ref = MU_STOP; ia.counter = h->dcnt + 0;
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel");
@@ -458,6 +467,83 @@ linmin_status linmin_destroy(linmin_handle h)
 }
 
 
+int linmin_get_lanes(linmin_handle h)
+{
+    return h ? h->bucket.G : -1;
+}
+
+linmin_status linmin_set_lanes(linmin_handle h, int lanes)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    Bucket c[16];
+    const int n = ipm_candidates(h->P, c, 16);
+    for (int i = 0; i < n; ++i)
+        if (c[i].G == lanes) { h->bucket = c[i]; return LINMIN_OK; }
+    return fail(h, LINMIN_ERR_UNSUPPORTED, "no compiled bucket with that many lanes for this P");
+}
+
+linmin_status linmin_autotune(linmin_handle h, const float *cube, long long N, const float *sigma,
+                              int *lanes_out, float *ms_out, int n_ms, int *n_candidates)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    if (!cube || !sigma || N < 1) return fail(h, LINMIN_ERR_INVALID, "cube, sigma, N >= 1");
+    const int L = h->L, P = h->P;
+    const long long n = N < 32768 ? N : 32768;
+    cudaStream_t st = h->stream;
+    const bool dev_cube = is_device_ptr(cube), dev_sigma = is_device_ptr(sigma);
+    if (!dev_sigma)
+        for (int l = 0; l < L; ++l)
+            if (!(sigma[l] > 0.f) || !std::isfinite(sigma[l]))
+                return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
+    linmin_status s;
+    if ((s = ensure_scratch(h, n)) != LINMIN_OK) return s;
+    if ((!dev_cube || !dev_sigma) && (s = ensure_io(h, n)) != LINMIN_OK) return s;
+    const float *d_cube = cube, *d_sigma = sigma;
+    if (!dev_cube) {
+        LM_CUDA(h, cudaMemcpyAsync(h->io_cube, cube, (size_t)n * L * 4, cudaMemcpyHostToDevice, st),
+                "copy cube");
+        d_cube = h->io_cube;
+    }
+    if (!dev_sigma) {
+        LM_CUDA(h, cudaMemcpyAsync(h->io_sigma, sigma, (size_t)L * 4, cudaMemcpyHostToDevice, st),
+                "copy sigma");
+        d_sigma = h->io_sigma;
+    }
+    Bucket cand[16];
+    const int nc = ipm_candidates(P, cand, 16);
+    if (n_candidates) *n_candidates = nc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LM_CUDA(h, cudaEventCreate(&e0), "event");
+    LM_CUDA(h, cudaEventCreate(&e1), "event");
+    int best = -1;
+    float best_ms = 3.4e38f;
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < nc && err == cudaSuccess; ++i) {
+        err = launch_prep(h->dS, d_sigma, L, P, cand[i].PP, h->prep, st);
+        if (err == cudaSuccess && i == 0)
+            err = launch_project(d_cube, n, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st);
+        float t_i = 3.4e38f;
+        for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+            err = cudaMemsetAsync(h->dcnt, 0, 8 * sizeof(unsigned long long), st);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+            if (err == cudaSuccess) err = launch_ipm(cand[i], false, ipm_args(h, n), st);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err == cudaSuccess && ms < t_i) t_i = ms;
+        }
+        if (ms_out && i < n_ms) ms_out[i] = t_i;
+        if (err == cudaSuccess && t_i < best_ms) { best_ms = t_i; best = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(h, err, "autotune");
+    if (best >= 0) h->bucket = cand[best];
+    if (lanes_out) *lanes_out = h->bucket.G;
+    return LINMIN_OK;
+}
+
 int linmin_last_launches(linmin_handle h)
 {
     return h ? h->launches : -1;
@@ -495,15 +581,16 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
         delete h;
         return cuda_fail(nullptr, a, "memory pool");
     }
-    const int PP = h->bucket.PP, PQ = pq_of(P);
+    const int PQ = pq_of(P);
 #define A(call) if (a == cudaSuccess) a = (call)
     A(dalloc(h, &h->dS, (size_t)P * L));
     A(dalloc(h, &h->prep.G64, (size_t)P * P));
     A(dalloc(h, &h->prep.Gt64, (size_t)P * P));
     A(dalloc(h, &h->prep.scale, 1));
-    A(dalloc(h, &h->prep.Ghi, (size_t)PP * PP));
-    A(dalloc(h, &h->prep.Glo, (size_t)PP * PP));
-    A(dalloc(h, &h->prep.grs, (size_t)PP));
+    // sized for the largest bucket: the handle may switch buckets (autotune)
+    A(dalloc(h, &h->prep.Ghi, (size_t)PP_MAX * PP_MAX));
+    A(dalloc(h, &h->prep.Glo, (size_t)PP_MAX * PP_MAX));
+    A(dalloc(h, &h->prep.grs, (size_t)PP_MAX));
     A(dalloc(h, &h->prep.gdiag, (size_t)P));
     A(dalloc(h, &h->prep.Bhi, (size_t)L * PQ));
     A(dalloc(h, &h->prep.Blo, (size_t)L * PQ));

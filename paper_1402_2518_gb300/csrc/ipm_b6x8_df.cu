@@ -1,0 +1,6 @@
+// Interior-point kernel, NS = 6 slots of G = 8 lanes per pixel (P <= 48),
+// double-float residual phase.
+#include "ipm_launch.cuh"
+namespace lm {
+template cudaError_t launch_ipm_mode<6, 8, true>(const IpmArgs &, cudaStream_t);
+}

@@ -39,5 +39,8 @@ LM_DECLARE_BUCKET(9, 4)
 LM_DECLARE_BUCKET(5, 8)
 LM_DECLARE_BUCKET(3, 16)
 LM_DECLARE_BUCKET(4, 16)
+LM_DECLARE_BUCKET(2, 8)
+LM_DECLARE_BUCKET(8, 4)
+LM_DECLARE_BUCKET(6, 8)
 
 }  // namespace lm

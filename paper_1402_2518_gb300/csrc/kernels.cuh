@@ -21,6 +21,9 @@ constexpr float SUPPORT_THETA = 0.01f;
 // Bucket of the interior-point kernel for a library size P.
 struct Bucket { int NS, G, PP; };
 bool ipm_bucket(int P, Bucket *b);
+// Compiled buckets that fit P (P <= PP < P + 16), at most max of them.
+int ipm_candidates(int P, Bucket *out, int max);
+constexpr int PP_MAX = 64;   // largest padded size of any bucket
 inline int pq_of(int P) { return ((P + 3) / 4) * 4; }
 
 // Device buffers produced by the library preparation (per sigma).

@@ -34,7 +34,8 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_unmix_noalloc", "linmin_last_launches", "linmin_phase_times_at",
             "linmin_server_default_options", "linmin_server_create", "linmin_server_submit",
             "linmin_server_poll", "linmin_server_wait", "linmin_server_get_stats",
-            "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes")
+            "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
+            "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
@@ -129,6 +130,14 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_phase_times_at.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                           ctypes.c_int]
     lib.linmin_phase_times_at.restype = ctypes.c_int
+    lib.linmin_get_lanes.argtypes = [H]
+    lib.linmin_get_lanes.restype = ctypes.c_int
+    lib.linmin_set_lanes.argtypes = [H, ctypes.c_int]
+    lib.linmin_set_lanes.restype = ctypes.c_int
+    lib.linmin_autotune.argtypes = [H, P, ctypes.c_longlong, P, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_int)]
+    lib.linmin_autotune.restype = ctypes.c_int
     lib.linmin_last_launches.argtypes = [H]
     lib.linmin_last_launches.restype = ctypes.c_int
     lib.linmin_version.argtypes = []
@@ -233,6 +242,26 @@ def linmin_unmix_noalloc(library, L: int, P: int, cube, N: int, sigma, abundance
     return lib().linmin_unmix_noalloc(_ptr(library), int(L), int(P), _ptr(cube), int(N),
                                       _ptr(sigma), _ptr(abundances), _ptr(uncertainties),
                                       _ptr(residual_rms), _ptr(iterations, "int32"), st)
+
+
+def linmin_get_lanes(h) -> int:
+    """Lanes per pixel of the handle's interior-point kernel."""
+    return lib().linmin_get_lanes(h)
+
+
+def linmin_set_lanes(h, lanes: int) -> int:
+    return _check(lib().linmin_set_lanes(h, int(lanes)), h)
+
+
+def linmin_autotune(h, cube, N: int, sigma) -> tuple[int, list]:
+    """Time every compiled bucket for the handle's P on a sample of the cube
+    and keep the fastest; returns (lanes per pixel, per-candidate ms)."""
+    lanes = ctypes.c_int(0)
+    n = ctypes.c_int(0)
+    ms = (ctypes.c_float * 16)()
+    _check(lib().linmin_autotune(h, _ptr(cube), int(N), _ptr(sigma), ctypes.byref(lanes), ms, 16,
+                                 ctypes.byref(n)), h)
+    return lanes.value, [float(ms[i]) for i in range(n.value)]
 
 
 def linmin_last_launches(h) -> int:

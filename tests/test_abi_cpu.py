@@ -144,3 +144,11 @@ def test_server_handle_bytes():
     assert b2 - b == 1000 * (16 * 36 + 44)
     assert bh - b == 1000 * (4 * 184 + 8 * 36 + 8) + 4 * 184
     assert pkg.linmin_server_handle_bytes(184, 65, 10) == 0
+
+
+def test_lanes_entry_points_reject_null_handle():
+    lib = pkg.load()
+    assert lib.linmin_get_lanes(None) == -1
+    assert lib.linmin_set_lanes(None, 4) == linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_autotune(None, None, 0, None, None, None, 0, None) == \
+        linmin.LINMIN_ERR_INVALID

@@ -42,3 +42,35 @@ def test_phase_ring_and_launch_count():
     st, _ = um.wait()
     assert st == 0
     um.close()
+
+
+def test_autotune_and_lanes():
+    """The autotuner picks one of the compiled buckets for P; every bucket
+    it may pick gives oracle-matching results."""
+    import oracle
+    import paper_1402_2518_gb300 as pkg
+    from paper_1402_2518_gb300 import linmin
+    pkg.load()
+    cube = synth.random_instance(4321, 6000, 184, 32, n_extras=4)
+    dev = torch.device("cuda:0")
+    um = pkg.Unmixer(torch.from_numpy(cube.S).to(dev))
+    X = torch.from_numpy(cube.X).to(dev)
+    sg = torch.from_numpy(cube.sigma).to(dev)
+    assert pkg.linmin_get_lanes(um.h) == 4                   # default for P = 32: 8 x 4
+    lanes, ms = pkg.linmin_autotune(um.h, X, cube.N, sg)
+    assert len(ms) >= 2 and all(t > 0 for t in ms)
+    assert lanes == pkg.linmin_get_lanes(um.h) and lanes in (4, 8)
+    rows = np.linspace(0, cube.N - 1, 200).astype(int)
+    ref = oracle.unmix(cube.S, cube.sigma, cube.X[rows])
+    for g in (4, 8):
+        pkg.linmin_set_lanes(um.h, g)
+        assert pkg.linmin_get_lanes(um.h) == g
+        x, sx, rms, it = um(X, sg)
+        st, _ = um.wait()
+        assert st == 0
+        assert np.abs(x.cpu().numpy()[rows] - ref["x"]).max() <= 1e-4
+    with pytest.raises(linmin.LinminError) as e:
+        pkg.linmin_set_lanes(um.h, 16)                        # no 16-lane bucket near P = 32
+    assert e.value.status == linmin.LINMIN_ERR_UNSUPPORTED
+    assert pkg.linmin_get_lanes(um.h) == 8                    # unchanged by the refusal
+    um.close()
