@@ -36,12 +36,13 @@ SPEC = synth.OMEGA_262K
 METRIC = "pixels/s IPLS unmix at <=1e-4 abs err vs FP64 oracle; served p50/p99 latency"
 FP32_LANES_PER_SM = 128
 
-# DRAM bytes per pixel of the two interior-point launches, from the ncu
-# capture summarised in profiles/ipm_refine_project_rms_omega65k_full.md
-# (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels).  Valid
-# only for the kernel source it was measured on (hash of csrc/ipm.cuh).
-IPM_TRAFFIC = {"ipm_sha256_12": "e5215b5b06b3",
-               "bytes_per_pixel": (9.756928e6 + 0.497408e6 + 38.651392e6 + 0.470016e6) / 65536}
+# DRAM bytes per pixel of the main interior-point launch, from the ncu
+# capture summarised in profiles/ipm_kernel_omega65k_full.md
+# (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels; traffic
+# grows with the pixel count).  Valid only for the kernel source it was
+# measured on (hash of csrc/ipm.cuh).
+IPM_TRAFFIC = {"ipm_sha256_12": "aaae08760011",
+               "bytes_per_pixel": (9.681152e6 + 0.081664e6) / 65536}
 
 
 def ipm_traffic(n_pix: int):
@@ -412,8 +413,8 @@ def main():
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": ipm_traffic(N),
-                     "traffic_note": "DRAM bytes per call of both IPM launches (ncu, scaled "
-                                     "from 65,536 pixels by pixel count)",
+                     "traffic_note": "DRAM bytes of the main IPM launch (ncu on 65,536 "
+                                     "pixels, scaled by pixel count)",
                      "peak_note": f"{nsm} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "flops_per_iter": flop_per_iter,
                      "mean_iters": float(iters.mean().item())},
