@@ -517,6 +517,363 @@ static cudaError_t launch_pass(const CrossArgs &a, cudaStream_t st)
     return launch_pass_t<64>(a, st);
 }
 
+// Crossover pass with a group of XG lanes per pixel.  The passes after the
+// first see only the pixels whose support changed (a few percent); one
+// thread per pixel would leave their time to the longest serial chain
+// (~1e5 double-float instructions for a 20-coordinate support).  Here row
+// r of L, and entry r of every vector indexed by the support, belong to
+// lane r % XG of the group; L (packed lower triangle, double-float) lives
+// in the group's shared memory.  Same arithmetic steps as
+// crossover_pass_kernel: Cholesky of G~_SS with the forward solves of 1
+// and c~_S fused in, nu from the bordered system, the back solve, the
+// decision, and on success x / sum(x) and the uncertainties, whose
+// diag(G~_SS^-1) comes from L^-1 formed in place (columns right to left).
+constexpr int XG = 8;
+
+template <int KMAX>
+struct XGCfg {
+    static constexpr int KS = (KMAX + XG - 1) / XG;        // row slots per lane
+    static constexpr int LSZ = KMAX * (KMAX + 1) / 2;      // packed lower triangle
+    static constexpr int THREADS = KMAX > 48 ? 32 : 64;    // 4 or 8 groups per block
+    static constexpr int GROUPS = THREADS / XG;
+    static constexpr int GROUP_WORDS = 2 * LSZ + 3 * KMAX; // L hi/lo, x hi/lo, support list
+    static size_t smem(int P) { return sizeof(float) * (2 * (size_t)P * P + (size_t)GROUPS * GROUP_WORDS); }
+};
+
+__device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }
+
+__device__ __forceinline__ df shfl_df(unsigned mask, df v, int src)
+{
+    return df{__shfl_sync(mask, v.hi, src, XG), __shfl_sync(mask, v.lo, src, XG)};
+}
+
+__device__ __forceinline__ df group_sum_df(unsigned mask, df v)
+{
+    for (int off = 1; off < XG; off <<= 1)
+        v = df_add(v, df{__shfl_xor_sync(mask, v.hi, off, XG), __shfl_xor_sync(mask, v.lo, off, XG)});
+    return v;
+}
+
+// smallest value, ties to the smallest index (index -1: no candidate)
+__device__ __forceinline__ void group_argmin(unsigned mask, float &v, int &i)
+{
+    for (int off = 1; off < XG; off <<= 1) {
+        const float ov = __shfl_xor_sync(mask, v, off, XG);
+        const int oi = __shfl_xor_sync(mask, i, off, XG);
+        if (oi >= 0 && (i < 0 || ov < v || (ov == v && oi < i))) { v = ov; i = oi; }
+    }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(XGCfg<KMAX>::THREADS)
+crossover_group_kernel(const CrossArgs a)
+{
+    using C = XGCfg<KMAX>;
+    constexpr int KS = C::KS;
+    extern __shared__ __align__(16) float sgm[];
+    const int P = a.P;
+    float *sGh = sgm, *sGl = sgm + P * P;
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int i = e / P, j = e % P;
+        sGh[e] = a.Ghi[(size_t)i * a.PP + j];
+        sGl[e] = a.Glo[(size_t)i * a.PP + j];
+    }
+    const int lane = threadIdx.x & 31, t = lane % XG, grp = threadIdx.x / XG;
+    const unsigned gmask = ((1u << XG) - 1u) << ((lane / XG) * XG);
+    float *Lh = sgm + 2 * P * P + (size_t)grp * C::GROUP_WORDS;
+    float *Ll = Lh + C::LSZ, *xh = Ll + C::LSZ, *xl = xh + KMAX;
+    int *sidx = reinterpret_cast<int *>(xl + KMAX);
+    __syncthreads();
+    const df zero = df_make(0.f);
+    const unsigned long long n_work = *a.len_in;
+    const long long stride = (long long)gridDim.x * C::GROUPS;
+    for (long long slot = (long long)blockIdx.x * C::GROUPS + grp; slot < (long long)n_work;
+         slot += stride) {
+        const long long n = a.list_in[slot];
+        const size_t base = (size_t)n * P;
+        const unsigned long long m = a.mask[n];
+        const int k = __popcll(m);
+        for (int i = t; i < P; i += XG)
+            if ((m >> i) & 1ULL) sidx[__popcll(m & ((1ULL << i) - 1ULL))] = i;
+        __syncwarp(gmask);
+        // L = G~_SS on the own rows; right-hand sides 1 and c~_S
+        df au[KS], av[KS], uu[KS], vv[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            const int r = s * XG + t;
+            au[s] = av[s] = uu[s] = vv[s] = zero;
+            if (r < k) {
+                const int gr = sidx[r];
+                for (int j = 0; j <= r; ++j) {
+                    const int gj = sidx[j];
+                    Lh[pk(r, j)] = sGh[gr * P + gj];
+                    Ll[pk(r, j)] = sGl[gr * P + gj];
+                }
+                au[s] = df_make(1.f);
+                av[s] = df{a.c_hi[base + gr], a.c_lo[base + gr]};
+            }
+        }
+        __syncwarp(gmask);
+        // right-looking Cholesky; the diagonal keeps 1/L_cc
+        bool ok = true;
+        for (int c = 0; c < k; ++c) {
+            df d = df{Lh[pk(c, c)], Ll[pk(c, c)]};
+            if (!(d.hi > 0.f)) { ok = false; d = df_make(1e-30f); }
+            const df rl = df_rsqrt(d);
+            df uc = zero, vc = zero, lrc[KS];
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const int r = s * XG + t;
+                lrc[s] = zero;
+                if (r > c && r < k) {
+                    lrc[s] = df_mul(df{Lh[pk(r, c)], Ll[pk(r, c)]}, rl);
+                    Lh[pk(r, c)] = lrc[s].hi;
+                    Ll[pk(r, c)] = lrc[s].lo;
+                }
+                if (r == c) {
+                    uc = df_mul(au[s], rl);
+                    vc = df_mul(av[s], rl);
+                    uu[s] = uc;
+                    vv[s] = vc;
+                    Lh[pk(c, c)] = rl.hi;
+                    Ll[pk(c, c)] = rl.lo;
+                }
+            }
+            uc = shfl_df(gmask, uc, c % XG);
+            vc = shfl_df(gmask, vc, c % XG);
+            __syncwarp(gmask);                       // column c of L stored
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const int r = s * XG + t;
+                if (r > c && r < k) {
+                    au[s] = df_fms(au[s], lrc[s], uc);
+                    av[s] = df_fms(av[s], lrc[s], vc);
+                }
+            }
+            // trailing update L_rj -= L_rc L_jc (c < j <= r): the lane's rows
+            // advance together (independent chains), L_jc read once per j
+            for (int j = c + 1; j < k; ++j) {
+                const df ljc = df{Lh[pk(j, c)], Ll[pk(j, c)]};
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    const int r = s * XG + t;
+                    if (r >= j && r < k) {
+                        const df v = df_fms(df{Lh[pk(r, j)], Ll[pk(r, j)]}, lrc[s], ljc);
+                        Lh[pk(r, j)] = v.hi;
+                        Ll[pk(r, j)] = v.lo;
+                    }
+                }
+            }
+            __syncwarp(gmask);                       // trailing block updated
+        }
+        // nu from the bordered system
+        df a11 = zero, a1b = zero;
+#pragma unroll
+        for (int s = 0; s < KS; ++s)
+            if (s * XG + t < k) {
+                a11 = df_add(a11, df_mul(uu[s], uu[s]));
+                a1b = df_add(a1b, df_mul(uu[s], vv[s]));
+            }
+        a11 = group_sum_df(gmask, a11);
+        a1b = group_sum_df(gmask, a1b);
+        const df nu = df_div(df_sub(a1b, df_make(1.f)), a11);
+        // back solve: xs = L^-T (v - nu u), ub = L^-T u (= G~_SS^-1 1)
+        df ax[KS], ab[KS], xs[KS], ub[KS];
+#pragma unroll
+        for (int s = 0; s < KS; ++s) {
+            ax[s] = df_fms(vv[s], nu, uu[s]);
+            ab[s] = uu[s];
+            xs[s] = ub[s] = zero;
+        }
+        for (int r = k - 1; r >= 0; --r) {
+            df xr = zero, ur = zero;
+#pragma unroll
+            for (int s = 0; s < KS; ++s)
+                if (s * XG + t == r) {
+                    const df rlr = df{Lh[pk(r, r)], Ll[pk(r, r)]};
+                    xr = df_mul(ax[s], rlr);
+                    ur = df_mul(ab[s], rlr);
+                    xs[s] = xr;
+                    ub[s] = ur;
+                }
+            xr = shfl_df(gmask, xr, r % XG);
+            ur = shfl_df(gmask, ur, r % XG);
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const int q = s * XG + t;
+                if (q < r) {
+                    const df lrq = df{Lh[pk(r, q)], Ll[pk(r, q)]};
+                    ax[s] = df_fms(ax[s], lrq, xr);
+                    ab[s] = df_fms(ab[s], lrq, ur);
+                }
+            }
+        }
+        // decision
+        int flip = -1;
+        df xsum = zero;
+        if (ok) {
+            float xmin = (float)-a.tol_x;
+            int fr = -1;
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const int r = s * XG + t;
+                if (r < k) {
+                    if (xs[s].hi < xmin) { xmin = xs[s].hi; fr = r; }
+                    if (xs[s].hi > 0.f) xsum = df_add(xsum, xs[s]);
+                }
+            }
+            group_argmin(gmask, xmin, fr);
+            xsum = group_sum_df(gmask, xsum);
+            if (fr >= 0) flip = (k == 1) ? -2 : sidx[fr];
+            if (flip == -1) {
+                // most negative multiplier off S, coordinates spread over the lanes
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    const int r = s * XG + t;
+                    if (r < k) { xh[r] = xs[s].hi; xl[r] = xs[s].lo; }
+                }
+                __syncwarp(gmask);
+                float lmin = (float)-a.tol_g;
+                int fi = -1;
+                for (int i = t; i < P; i += XG) {
+                    if ((m >> i) & 1ULL) continue;
+                    dot2 g;
+                    for (int q = 0; q < k; ++q) {
+                        const float gh = sGh[i * P + sidx[q]], gl = sGl[i * P + sidx[q]];
+                        g.add_prod(gh, xh[q]);
+                        g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+                    }
+                    g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
+                    g.add_df(nu);
+                    const df gv = g.result();
+                    if (gv.hi < lmin) { lmin = gv.hi; fi = i; }
+                }
+                group_argmin(gmask, lmin, fi);
+                flip = fi;
+            }
+        } else {
+            flip = -2;
+        }
+        if (flip == -1 && xsum.hi > 0.f) {
+            // KKT holds: abundances and uncertainties
+            for (int i = t; i < P; i += XG)
+                if (!((m >> i) & 1ULL)) a.x_out[base + i] = 0.f;
+#pragma unroll
+            for (int s = 0; s < KS; ++s) {
+                const int r = s * XG + t;
+                if (r < k) a.x_out[base + sidx[r]] = xs[s].hi > 0.f ? df_div(xs[s], xsum).hi : 0.f;
+            }
+            if (a.sx_out) {
+                // L -> L^-1 in place: Linv_ij = -(sum_{j<q<=i} Linv_iq L_qj) / L_jj,
+                // column j from right to left (rows on their lanes)
+                for (int j = k - 2; j >= 0; --j) {
+                    const df rlj = df{Lh[pk(j, j)], Ll[pk(j, j)]};
+                    df acc[KS];
+#pragma unroll
+                    for (int s = 0; s < KS; ++s) acc[s] = zero;
+                    for (int q = j + 1; q < k; ++q) {
+                        const df lqj = df{Lh[pk(q, j)], Ll[pk(q, j)]};
+#pragma unroll
+                        for (int s = 0; s < KS; ++s) {
+                            const int i = s * XG + t;
+                            if (i >= q && i < k)
+                                acc[s] = df_fms(acc[s], df{Lh[pk(i, q)], Ll[pk(i, q)]}, lqj);
+                        }
+                    }
+                    __syncwarp(gmask);               // column j read by every row
+#pragma unroll
+                    for (int s = 0; s < KS; ++s) {
+                        const int i = s * XG + t;
+                        if (i > j && i < k) {
+                            const df v = df_mul(acc[s], rlj);
+                            Lh[pk(i, j)] = v.hi;
+                            Ll[pk(i, j)] = v.lo;
+                        }
+                    }
+                    __syncwarp(gmask);
+                }
+                const float sc = (float)a.scale[0];
+                const df inv_a11 = df_div(df_make(1.f), a11);
+                for (int i = t; i < P; i += XG)
+                    if (!((m >> i) & 1ULL)) a.sx_out[base + i] = 0.f;
+                df nrm[KS];
+#pragma unroll
+                for (int s = 0; s < KS; ++s) nrm[s] = zero;
+                for (int i = t; i < k; ++i) {
+#pragma unroll
+                    for (int s = 0; s < KS; ++s) {
+                        const int j = s * XG + t;
+                        if (j <= i) {
+                            const df w = df{Lh[pk(i, j)], Ll[pk(i, j)]};
+                            nrm[s] = df_add(nrm[s], df_mul(w, w));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    const int j = s * XG + t;
+                    if (j < k) {
+                        const df var = df_sub(nrm[s], df_mul(df_mul(ub[s], ub[s]), inv_a11));
+                        a.sx_out[base + sidx[j]] = sqrtf(fmaxf(var.hi, 0.f) / sc);
+                    }
+                }
+            }
+        } else if (flip >= 0 && a.list_out) {
+            if (t == 0) {
+                a.mask[n] = m ^ (1ULL << flip);
+                const unsigned long long pos = atomicAdd(a.len_out, 1ULL);
+                a.list_out[pos] = n;
+            }
+        } else {
+            // not finished here: retry list, or (retry path) keep the iterate
+            if (t == 0) {
+                if (a.retry_list) {
+                    const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
+                    a.retry_list[pos] = n;
+                } else if (a.n_unverified) {
+                    atomicAdd(a.n_unverified, 1ULL);
+                }
+            }
+            for (int i = t; i < P; i += XG) {
+                if (a.x_out != a.x_in) a.x_out[base + i] = a.x_in[base + i];
+                if (a.sx_out) a.sx_out[base + i] = 0.f;
+            }
+        }
+        __syncwarp(gmask);                           // the group's shared memory is reused
+    }
+}
+
+template <int KMAX>
+static cudaError_t launch_group_t(const CrossArgs &a, cudaStream_t st)
+{
+    using C = XGCfg<KMAX>;
+    const size_t smem = C::smem(a.P);
+    cudaError_t e = cudaFuncSetAttribute(crossover_group_kernel<KMAX>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, crossover_group_kernel<KMAX>, C::THREADS,
+                                                  smem);
+    if (per_sm < 1) per_sm = 1;
+    // the list length is on the device: one wave of groups striding over it,
+    // at most one group per list entry
+    long long blocks = (long long)sms * per_sm;
+    const long long need = (a.N + C::GROUPS - 1) / C::GROUPS;
+    if (blocks > need) blocks = need;
+    crossover_group_kernel<KMAX><<<(unsigned)blocks, C::THREADS, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_pass_group(const CrossArgs &a, cudaStream_t st)
+{
+    if (a.P <= 16) return launch_group_t<16>(a, st);
+    if (a.P <= 32) return launch_group_t<32>(a, st);
+    if (a.P <= 48) return launch_group_t<48>(a, st);
+    return launch_group_t<64>(a, st);
+}
+
 cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
                              const long long *list, const unsigned long long *list_len,
                              cudaStream_t st)
@@ -555,7 +912,9 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
         const bool last = pass == MAX_SWAPS;
         a.list_out = last ? nullptr : w.list[(pass + 1) & 1];
         a.len_out = last ? nullptr : w.len + pass + 1;
-        e = launch_pass(a, st);
+        // pass 0 over the whole cube is throughput bound: thread per pixel;
+        // every other pass holds few pixels and is latency bound: lane groups
+        e = (pass == 0 && !list) ? launch_pass(a, st) : launch_pass_group(a, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
