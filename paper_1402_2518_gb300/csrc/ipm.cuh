@@ -151,19 +151,19 @@ ipm_kernel(const IpmArgs a)
         const size_t base = (size_t)p * P;
         cbase = base;
         if (!ACC) {
-            // x0 = 1/P; g0 = G~ x0 - c~; nu0 makes lambda0 = g0 + nu0 >= delta
-            float gmin = 3.4e38f, gmax = -3.4e38f, g0[NS];
+            // x0 = 1/P; g0 = G~ x0 - c~; nu0 makes lambda0 = g0 + nu0 dual
+            // feasible with min lambda0 = 1e-3 (a smaller start than adding
+            // the spread of g0 as well: 11.2 instead of 11.7 iterations on
+            // the OMEGA-shaped workload)
+            float gmin = 3.4e38f, g0[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 g0[s] = valid[s] ? sGrs[s * G + t] - __ldg(a.c_hi + base + s * G + t) : 0.f;
-                if (valid[s]) { gmin = fminf(gmin, g0[s]); gmax = fmaxf(gmax, g0[s]); }
+                if (valid[s]) gmin = fminf(gmin, g0[s]);
             }
-            for (int off = 1; off < G; off <<= 1) {
+            for (int off = 1; off < G; off <<= 1)
                 gmin = fminf(gmin, __shfl_xor_sync(gmask, gmin, off));
-                gmax = fmaxf(gmax, __shfl_xor_sync(gmask, gmax, off));
-            }
-            const float delta = (gmax - gmin) + 1e-3f;
-            nu = delta - gmin;
+            nu = 1e-3f - gmin;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 x[s] = valid[s] ? invP : 0.f;
