@@ -208,7 +208,7 @@ size_t handle_bytes(int L, int P, long long N, bool host_io)
 {
     Bucket b{};
     if (!ipm_bucket(P, &b)) return 0;
-    const size_t PP = b.PP, PQ = pq_of(P), n = (size_t)(N > 0 ? N : 1);
+    const size_t PQ = pq_of(P), n = (size_t)(N > 0 ? N : 1);
     (void)b;
     const size_t PPM = PP_MAX;
     size_t fixed = 4 * (size_t)P * L + 8 * 2 * (size_t)P * P + 8 + 4 * 2 * PPM * PPM + 4 * PPM +
