@@ -185,6 +185,42 @@ def unmix(S, sigma, X, nthreads: int = 0, max_iter: int = MAX_ITER,
     return out
 
 
+def unmix_cov(S, cov_inv, X, max_iter: int = MAX_ITER):
+    """Unmixing under a full noise covariance C (Sec. 2.3, eq.
+    RenormalizedProblem: the data are whitened as X' = X L with
+    C^-1 = L L^T).  The whitened criterion ||L^T (y - S^T x)||^2 has the
+    Gram G = S C^-1 S^T and the projection c = S C^-1 y; each pixel is then
+    the same fully constrained problem as with a diagonal C, solved by
+    ``fcls`` (fp64), with the uncertainty of ``sigma_x`` on the support of
+    ``support`` and the unwhitened RMS of ``rms``.  G and c are formed in
+    fp64 (numpy); there is no per-band sigma.
+
+    Returns dict(x, sx, rms, iters) like ``unmix``."""
+    S32, X32 = _f32(S), _f32(X)
+    S64, X64 = S32.astype(np.float64), X32.astype(np.float64)
+    Ci = np.asarray(cov_inv, dtype=np.float64)
+    P, L = S64.shape
+    if Ci.shape != (L, L) or X64.shape[1] != L:
+        raise ValueError("shape mismatch between S, cov_inv and X")
+    T = Ci @ S64.T                 # L x P
+    G = S64 @ T                    # S C^-1 S^T
+    Cp = X64 @ T                   # rows: c = S C^-1 y
+    sy = np.einsum("nl,lm,nm->n", X64, Ci, X64)
+    N = X64.shape[0]
+    out = dict(x=np.empty((N, P)), sx=np.empty((N, P)), rms=np.empty(N),
+               iters=np.empty(N, dtype=np.int32))
+    for n in range(N):
+        r = fcls(G, Cp[n], sy[n], max_iter)
+        x = np.maximum(r["x"], 0.0)
+        x /= x.sum()
+        m = support(G, r["x"], r["lam"])
+        out["x"][n] = x
+        out["sx"][n] = sigma_x(G, m)
+        out["rms"][n] = rms(S32, x, X32[n])
+        out["iters"][n] = r["iters"] if r["status"] == OR_OK else -r["iters"]
+    return out
+
+
 def objective(G, c, s, x):
     """f(x) = 1/2 x'Gx - c'x + s/2 in fp64 (the whitened half squared error)."""
     x = np.asarray(x, dtype=np.float64)

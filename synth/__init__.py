@@ -232,3 +232,37 @@ def poisson_arrivals(n: int, rate_per_s: float = 200.0,
     """Arrival times (s) of a Poisson stream of ``n`` requests."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+# ------------------------------------------------------ full covariance
+def ar1_covariance(sigma: np.ndarray, rho: float) -> np.ndarray:
+    """C = D R D with D = diag(sigma) and R_lm = rho^|l - m|: noise whose
+    neighbouring bands are correlated (the off-diagonal terms of Sec. 2.3),
+    L x L float64."""
+    sg = np.asarray(sigma, dtype=np.float64)
+    idx = np.arange(sg.shape[0])
+    R = float(rho) ** np.abs(idx[:, None] - idx[None, :])
+    return sg[:, None] * R * sg[None, :]
+
+
+def make_cube_cov(spec: CubeSpec, rho: float, n_pix: int | None = None):
+    """The cube of ``spec`` (same library, sigma and abundances) with noise
+    drawn from the AR(1) covariance of ``ar1_covariance(sigma, rho)``.
+    Returns (cube, C, C^-1)."""
+    base = make_cube(spec, n_pix=1)
+    S, sigma = base.S.astype(np.float64), base.sigma.astype(np.float64)
+    N = spec.n_pix if n_pix is None else min(int(n_pix), spec.n_pix)
+    prng = np.random.Generator(np.random.PCG64(spec.seed + 7919))
+    A = abundances(prng, spec.n_pix, spec.P, spec.n_minerals, spec.kmax,
+                   spec.pure_frac)[:N]
+    C = ar1_covariance(sigma, rho)
+    Lc = np.linalg.cholesky(C)
+    nrng = np.random.Generator(np.random.PCG64(spec.seed + 15485863))
+    X = np.empty((N, spec.L), dtype=np.float32)
+    for lo in range(0, N, 65536):
+        hi = min(N, lo + 65536)
+        E = nrng.standard_normal((hi - lo, spec.L)) @ Lc.T
+        X[lo:hi] = (A[lo:hi] @ S + E).astype(np.float32)
+    Cinv = np.linalg.inv(C)
+    Cinv = 0.5 * (Cinv + Cinv.T)
+    return Cube(spec, base.S, base.sigma, X, A), C, Cinv
