@@ -152,6 +152,26 @@ LINMIN_API linmin_status linmin_unmix(linmin_handle h, const float *cube, long l
                            float *uncertainties, float *residual_rms,
                            int *iterations);
 
+/*
+ * linmin_unmix under a full noise covariance C (Sec. 2.3, eq.
+ * RenormalizedProblem: the data are whitened as X' = X L with C^-1 = L L^T;
+ * off-diagonal terms model band-correlated noise).
+ *   cov_inv  the L x L inverse covariance C^-1, symmetric positive definite,
+ *            row-major float64, host or device.  It is copied to the host
+ *            and checked (finite, symmetric to 1e-9 of its largest entry,
+ *            positive definite by an fp64 Cholesky) whenever its contents
+ *            differ from the last checked one (LINMIN_ERR_INVALID
+ *            otherwise); its symmetric part is used.
+ * G = S C^-1 S^T and B = C^-1 S^T are formed in fp64 on the device; the
+ * projection, the solve, the uncertainties (from G) and the unwhitened RMS
+ * are those of linmin_unmix.  Other arguments and the return value as
+ * linmin_unmix.  The handle keeps C^-1 (L^2 doubles) on the device.
+ */
+LINMIN_API linmin_status linmin_unmix_cov(linmin_handle h, const float *cube, long long N,
+                                          const double *cov_inv, float *abundances,
+                                          float *uncertainties, float *residual_rms,
+                                          int *iterations);
+
 /* Synchronise the handle's stream.  *n_not_converged (may be NULL) receives
  * the number of pixels of the last linmin_unmix that hit max_iter.  Returns
  * LINMIN_ERR_NOT_CONVERGED when that number is non-zero. */

@@ -195,7 +195,7 @@ def unmix_cov(S, cov_inv, X, max_iter: int = MAX_ITER):
     ``support`` and the unwhitened RMS of ``rms``.  G and c are formed in
     fp64 (numpy); there is no per-band sigma.
 
-    Returns dict(x, sx, rms, iters) like ``unmix``."""
+    Returns dict(x, sx, rms, iters, lam) like ``unmix``, and the Gram G."""
     S32, X32 = _f32(S), _f32(X)
     S64, X64 = S32.astype(np.float64), X32.astype(np.float64)
     Ci = np.asarray(cov_inv, dtype=np.float64)
@@ -208,9 +208,10 @@ def unmix_cov(S, cov_inv, X, max_iter: int = MAX_ITER):
     sy = np.einsum("nl,lm,nm->n", X64, Ci, X64)
     N = X64.shape[0]
     out = dict(x=np.empty((N, P)), sx=np.empty((N, P)), rms=np.empty(N),
-               iters=np.empty(N, dtype=np.int32))
+               iters=np.empty(N, dtype=np.int32), lam=np.empty((N, P)), G=G)
     for n in range(N):
         r = fcls(G, Cp[n], sy[n], max_iter)
+        out["lam"][n] = r["lam"]
         x = np.maximum(r["x"], 0.0)
         x /= x.sum()
         m = support(G, r["x"], r["lam"])

@@ -63,6 +63,10 @@ struct linmin_ctx {
     cudaEvent_t ev[LINMIN_PHASE_RING][LINMIN_NUM_PHASES + 1] = {};
     long long calls = 0;          // profiled calls so far (ring position)
     int launches = 0;            // kernel launches of the last linmin_unmix
+    // full noise covariance (linmin_unmix_cov): C^-1 on the device, the
+    // T = C^-1 S^T scratch, and the hash of the C^-1 last checked
+    double *cov = nullptr, *covT = nullptr;
+    unsigned long long cov_hash = 0;
     cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
 };
 
@@ -318,21 +322,80 @@ static linmin_status ensure_io(linmin_ctx *h, long long N)
     return LINMIN_OK;
 }
 
-linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, const float *sigma,
-                           float *abundances, float *uncertainties, float *residual_rms,
-                           int *iterations)
+// C^-1 of linmin_unmix_cov: copied to the host, checked (finite,
+// symmetric, positive definite by an fp64 Cholesky) and uploaded when its
+// contents differ from the last checked one.
+static linmin_status load_cov(linmin_ctx *h, const double *cov_inv)
+{
+    const int L = h->L;
+    const size_t n = (size_t)L * L;
+    std::vector<double> c(n);
+    if (is_device_ptr(cov_inv)) {
+        LM_CUDA(h, cudaMemcpy(c.data(), cov_inv, n * 8, cudaMemcpyDeviceToHost), "copy cov_inv");
+    } else {
+        std::memcpy(c.data(), cov_inv, n * 8);
+    }
+    unsigned long long hsh = 1469598103934665603ULL;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(c.data());
+    for (size_t i = 0; i < n * 8; ++i) { hsh ^= b[i]; hsh *= 1099511628211ULL; }
+    if (h->cov && hsh == h->cov_hash) return LINMIN_OK;
+    double amax = 0.0;
+    for (double v : c) {
+        if (!std::isfinite(v)) return fail(h, LINMIN_ERR_INVALID, "cov_inv has NaN/Inf");
+        amax = std::fmax(amax, std::fabs(v));
+    }
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < i; ++j)
+            if (std::fabs(c[(size_t)i * L + j] - c[(size_t)j * L + i]) > 1e-9 * amax)
+                return fail(h, LINMIN_ERR_INVALID, "cov_inv is not symmetric");
+    // symmetric part, then its Cholesky as the positive-definiteness test
+    std::vector<double> sym(n), f(n);
+    for (int i = 0; i < L; ++i)
+        for (int j = 0; j < L; ++j)
+            sym[(size_t)i * L + j] = 0.5 * (c[(size_t)i * L + j] + c[(size_t)j * L + i]);
+    f = sym;
+    for (int k = 0; k < L; ++k) {
+        double d = f[(size_t)k * L + k];
+        for (int q = 0; q < k; ++q) d -= f[(size_t)k * L + q] * f[(size_t)k * L + q];
+        if (!(d > 0.0)) return fail(h, LINMIN_ERR_INVALID, "cov_inv is not positive definite");
+        d = std::sqrt(d);
+        f[(size_t)k * L + k] = d;
+        for (int i = k + 1; i < L; ++i) {
+            double v = f[(size_t)i * L + k];
+            for (int q = 0; q < k; ++q) v -= f[(size_t)i * L + q] * f[(size_t)k * L + q];
+            f[(size_t)i * L + k] = v / d;
+        }
+    }
+    cudaError_t a = cudaSuccess;
+    if (!h->cov) {
+        a = dalloc(h, &h->cov, n);
+        if (a == cudaSuccess) a = dalloc(h, &h->covT, (size_t)L * h->P);
+        if (a != cudaSuccess) { h->cov = h->covT = nullptr; return cuda_fail(h, a, "cov allocation"); }
+    }
+    LM_CUDA(h, cudaMemcpyAsync(h->cov, sym.data(), n * 8, cudaMemcpyHostToDevice, h->stream),
+            "upload cov_inv");
+    LM_CUDA(h, cudaStreamSynchronize(h->stream), "upload cov_inv");
+    h->cov_hash = hsh;
+    return LINMIN_OK;
+}
+
+// linmin_unmix (sigma) and linmin_unmix_cov (cov_inv): exactly one is set
+static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
+                                const double *cov_inv, float *abundances, float *uncertainties,
+                                float *residual_rms, int *iterations)
 {
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
     if (N < 0) return fail(h, LINMIN_ERR_INVALID, "N < 0");
     h->launches = 0;
     if (N == 0) return LINMIN_OK;
-    if (!cube || !sigma) return fail(h, LINMIN_ERR_INVALID, "cube or sigma is NULL");
+    if (!cube || (!sigma && !cov_inv))
+        return fail(h, LINMIN_ERR_INVALID, sigma || cov_inv ? "cube is NULL" : "sigma is NULL");
     if (N > (1LL << 40)) return fail(h, LINMIN_ERR_INVALID, "N too large");
     const int L = h->L, P = h->P;
     cudaStream_t st = h->stream;
     LM_CUDA(h, cudaSetDevice(h->device), "cudaSetDevice");
 
-    const bool dev_cube = is_device_ptr(cube), dev_sigma = is_device_ptr(sigma);
+    const bool dev_cube = is_device_ptr(cube), dev_sigma = !sigma || is_device_ptr(sigma);
     const bool dev_out[4] = {!abundances || is_device_ptr(abundances),
                              !uncertainties || is_device_ptr(uncertainties),
                              !residual_rms || is_device_ptr(residual_rms),
@@ -345,6 +408,7 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
                 return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
     }
     linmin_status s;
+    if (cov_inv && (s = load_cov(h, cov_inv)) != LINMIN_OK) return s;
     if ((s = ensure_scratch(h, N)) != LINMIN_OK) return s;
     if (host_any && (s = ensure_io(h, N)) != LINMIN_OK) return s;
 
@@ -368,7 +432,11 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     LM_CUDA(h, cudaMemsetAsync(h->prep.flags, 0, sizeof(int), st), "memset");
     LM_CUDA(h, cudaMemsetAsync(h->dcnt, 0, 8 * sizeof(unsigned long long), st), "memset");
     mark(h, 0);
-    LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
+    if (cov_inv)
+        LM_CUDA(h, launch_prep_cov(h->dS, h->cov, L, P, h->bucket.PP, h->prep, h->covT, st),
+                "prep kernels");
+    else
+        LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
     mark(h, 1);
     LM_CUDA(h, launch_project(d_cube, N, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st),
             "projection kernel");
@@ -402,8 +470,8 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
     if (h->opt.profile) ++h->calls;
-    h->launches = PREP_LAUNCHES + 1 + 1 + crossover_launches(true) + 2 + crossover_launches(false) +
-                  (d_rms ? 1 : 0);
+    h->launches = (cov_inv ? PREP_COV_LAUNCHES : PREP_LAUNCHES) + 1 + 1 + crossover_launches(true) +
+                  2 + crossover_launches(false) + (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
                       "copy iterations");
 
@@ -419,6 +487,24 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
         LM_CUDA(h, cudaMemcpyAsync(iterations, d_it, (size_t)N * 4, cudaMemcpyDeviceToHost, st),
                 "copy iterations");
     return linmin_wait(h, nullptr);
+}
+
+linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, const float *sigma,
+                           float *abundances, float *uncertainties, float *residual_rms,
+                           int *iterations)
+{
+    if (h && N > 0 && !sigma) return fail(h, LINMIN_ERR_INVALID, "sigma is NULL");
+    return unmix_impl(h, cube, N, sigma, nullptr, abundances, uncertainties, residual_rms,
+                      iterations);
+}
+
+linmin_status linmin_unmix_cov(linmin_handle h, const float *cube, long long N,
+                               const double *cov_inv, float *abundances, float *uncertainties,
+                               float *residual_rms, int *iterations)
+{
+    if (h && N > 0 && !cov_inv) return fail(h, LINMIN_ERR_INVALID, "cov_inv is NULL");
+    return unmix_impl(h, cube, N, nullptr, cov_inv, abundances, uncertainties, residual_rms,
+                      iterations);
 }
 
 linmin_status linmin_wait(linmin_handle h, long long *n_not_converged)
@@ -490,7 +576,7 @@ linmin_status linmin_autotune(linmin_handle h, const float *cube, long long N, c
     const int L = h->L, P = h->P;
     const long long n = N < 32768 ? N : 32768;
     cudaStream_t st = h->stream;
-    const bool dev_cube = is_device_ptr(cube), dev_sigma = is_device_ptr(sigma);
+    const bool dev_cube = is_device_ptr(cube), dev_sigma = !sigma || is_device_ptr(sigma);
     if (!dev_sigma)
         for (int l = 0; l < L; ++l)
             if (!(sigma[l] > 0.f) || !std::isfinite(sigma[l]))
@@ -628,7 +714,7 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
                     h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
                     h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
-                    h->io_x, h->io_sx, h->io_rms, h->io_it};
+                    h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     if (h->pool) pool_release(h->device);

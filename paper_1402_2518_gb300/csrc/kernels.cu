@@ -120,6 +120,79 @@ cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP
     return cudaGetLastError();
 }
 
+// --------------------------------------------------- prep, full covariance
+// Sec. 2.3 with a full noise covariance C: the whitened Gram is
+// G = S C^-1 S^T and the projection operator B = C^-1 S^T (fp64).
+// T = C^-1 S^T (L x P, row-major [l][j]): thread per entry.
+__global__ void prep_t_kernel(const float *__restrict__ S, const double *__restrict__ Cinv,
+                              int L, int P, double *__restrict__ T)
+{
+    const long long total = (long long)L * P;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(e / P), j = (int)(e % P);
+        const double *crow = Cinv + (size_t)l * L;
+        const float *srow = S + (size_t)j * L;
+        double acc = 0.0;
+        for (int m = 0; m < L; ++m) acc = fma(crow[m], (double)srow[m], acc);
+        T[e] = acc;
+    }
+}
+
+// G_ij = sum_l S_il T_lj: warp per pair of the lower triangle
+__global__ void prep_gram_cov_kernel(const float *__restrict__ S, const double *__restrict__ T,
+                                     int L, int P, double *__restrict__ G64)
+{
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int npairs = P * (P + 1) / 2;
+    if (wid >= npairs) return;
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= wid) ++i;
+    const int j = wid - i * (i + 1) / 2;
+    double acc = 0.0;
+    for (int l = lane; l < L; l += 32) acc = fma((double)S[(size_t)i * L + l], T[(size_t)l * P + j], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        G64[(size_t)i * P + j] = acc;
+        G64[(size_t)j * P + i] = acc;
+    }
+}
+
+// B~ = T / s as hi + lo float32, [l][j] padded to PQ columns
+__global__ void prep_b_cov_kernel(const double *__restrict__ T, int L, int P, int PQ,
+                                  const double *__restrict__ scale, float *__restrict__ Bhi,
+                                  float *__restrict__ Blo)
+{
+    const double s = scale[0];
+    const long long total = (long long)L * PQ;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int l = (int)(e / PQ), j = (int)(e % PQ);
+        const df d = split_double(j < P ? T[(size_t)l * P + j] / s : 0.0);
+        Bhi[e] = d.hi;
+        Blo[e] = d.lo;
+    }
+}
+
+cudaError_t launch_prep_cov(const float *S, const double *Cinv, int L, int P, int PP,
+                            const Prep &o, double *T, cudaStream_t st)
+{
+    const long long lp = (long long)L * P;
+    const int tb = (int)((lp + 255) / 256 < 1024 ? (lp + 255) / 256 : 1024);
+    prep_t_kernel<<<tb, 256, 0, st>>>(S, Cinv, L, P, T);
+    const int npairs = P * (P + 1) / 2;
+    const int threads = 256, wpb = threads / 32;
+    prep_gram_cov_kernel<<<(npairs + wpb - 1) / wpb, threads, 0, st>>>(S, T, L, P, o.G64);
+    prep_finish_kernel<<<1, 256, 0, st>>>(P, PP, o.G64, o.Gt64, o.scale, o.Ghi, o.Glo,
+                                          o.grs, o.gdiag, o.flags);
+    const int PQ = pq_of(P);
+    const long long total = (long long)L * PQ;
+    const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
+    prep_b_cov_kernel<<<blocks, 256, 0, st>>>(T, L, P, PQ, o.scale, o.Bhi, o.Blo);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ projection
 constexpr int PROJ_THREADS = 128;
 

@@ -41,10 +41,14 @@ struct Prep {
 // kernel launches issued by launch_prep and launch_crossover (kept next to
 // them so that the launch count the C ABI reports stays exact)
 constexpr int PREP_LAUNCHES = 3;
+constexpr int PREP_COV_LAUNCHES = 4;
 constexpr int crossover_launches(bool whole_cube) { return (whole_cube ? 3 : 1) + MAX_SWAPS + 1; }
 
 cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP,
                         const Prep &o, cudaStream_t st);
+// Full noise covariance: C^-1 (L x L fp64, device), T scratch (L x P fp64).
+cudaError_t launch_prep_cov(const float *S, const double *Cinv, int L, int P, int PP,
+                            const Prep &o, double *T, cudaStream_t st);
 cudaError_t launch_project(const float *cube, long long N, int L, int P,
                            const float *Bhi, const float *Blo, float *c_hi,
                            float *c_lo, cudaStream_t st);

@@ -35,7 +35,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_server_default_options", "linmin_server_create", "linmin_server_submit",
             "linmin_server_poll", "linmin_server_wait", "linmin_server_get_stats",
             "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
-            "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune")
+            "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
@@ -94,6 +94,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_create.restype = ctypes.c_int
     lib.linmin_unmix.argtypes = [H, P, ctypes.c_longlong, P, P, P, P, P]
     lib.linmin_unmix.restype = ctypes.c_int
+    lib.linmin_unmix_cov.argtypes = [H, P, ctypes.c_longlong, P, P, P, P, P]
+    lib.linmin_unmix_cov.restype = ctypes.c_int
     lib.linmin_wait.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
     lib.linmin_wait.restype = ctypes.c_int
     lib.linmin_phase_times.argtypes = [H, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
@@ -200,6 +202,17 @@ def linmin_unmix(h, cube, N: int, sigma, abundances=None, uncertainties=None,
     st = lib().linmin_unmix(h, _ptr(cube), int(N), _ptr(sigma), _ptr(abundances),
                             _ptr(uncertainties), _ptr(residual_rms),
                             _ptr(iterations, "int32"))
+    if check and st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
+        _check(st, h)
+    return st
+
+
+def linmin_unmix_cov(h, cube, N: int, cov_inv, abundances=None, uncertainties=None,
+                     residual_rms=None, iterations=None, check: bool = True) -> int:
+    """linmin_unmix under a full noise covariance (cov_inv: L x L float64)."""
+    st = lib().linmin_unmix_cov(h, _ptr(cube), int(N), _ptr(cov_inv, "float64"),
+                                _ptr(abundances), _ptr(uncertainties), _ptr(residual_rms),
+                                _ptr(iterations, "int32"))
     if check and st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
         _check(st, h)
     return st
