@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-cov", action="store_true", help="skip the full-covariance leg")
+    ap.add_argument("--precision", default="tc", choices=["df", "tc", "bf16"],
+                    help="projection: double-float CUDA cores, exact tensor-core slices, bf16")
     ap.add_argument("--serving-cubes", type=int, default=64)
     ap.add_argument("--serving-rate", type=float, default=200.0, help="arrivals per second")
     ap.add_argument("--serving-budget-gb", type=float, default=120.0)
@@ -161,7 +163,7 @@ def cpu_baseline(cube, target_s: float):
             "sample": f"first {n} of {cube.N} pixels of {SPEC.name}, {dt:.1f} s"}
 
 
-def run_e2e(pkg, cube, steps):
+def run_e2e(pkg, cube, steps, precision=0):
     """Seconds per step of linmin_unmix on pinned host buffers: the cube and
     sigma are copied in and every output copied back inside the call."""
     import torch
@@ -172,7 +174,9 @@ def run_e2e(pkg, cube, steps):
     sxh = torch.empty((N, P)).pin_memory()
     rh = torch.empty((N,)).pin_memory()
     ih = torch.empty((N,), dtype=torch.int32).pin_memory()
-    h = pkg.linmin_create(cube.S, L, P)
+    opt = pkg.linmin_default_options()
+    opt.precision = precision
+    h = pkg.linmin_create(cube.S, L, P, opt)
 
     def step():
         pkg.linmin_unmix(h, Xh.numpy(), N, sgh.numpy(), xh.numpy(), sxh.numpy(),
@@ -350,7 +354,9 @@ def main():
     import paper_1402_2518_gb300 as pkg
     pkg.load()
     stream = torch.cuda.Stream(device=dev)
-    um = pkg.Unmixer(torch.from_numpy(cube.S).to(dev), stream=stream, profile=True)
+    prec = {"df": 0, "tc": 1, "bf16": 2}[args.precision]
+    um = pkg.Unmixer(torch.from_numpy(cube.S).to(dev), stream=stream, profile=True,
+                     precision=prec)
     X = torch.from_numpy(cube.X).to(dev)
     sig = torch.from_numpy(cube.sigma).to(dev)
     N, P, L = cube.N, cube.P, cube.L
@@ -403,7 +409,7 @@ def main():
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e_s = e2e = None
     if not args.no_e2e:
-        e2e_s = run_e2e(pkg, cube, max(3, args.steps // 2))
+        e2e_s = run_e2e(pkg, cube, max(3, args.steps // 2), prec)
         if ws > 1:
             t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -436,7 +442,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (double-float projection and crossover)",
+        "dtype": {"df": "f32 (double-float projection and crossover)",
+                  "tc": "f32 (bf16 tensor-core projection on exact 8-bit slices, "
+                        "double-float crossover)",
+                  "bf16": "f32 (bf16 tensor-core projection, double-float crossover)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": SPEC.name, "pixels": N, "L": L, "P": P,
                    "library": "32 minerals + 4 level/slope spectra",

@@ -77,10 +77,18 @@ typedef enum {
     LINMIN_ERR_UNSUPPORTED = 7     /* P or L outside the built kernel range */
 } linmin_status;
 
-/* Projection precision (c = S W^2 y).  LINMIN_PROJ_DF accumulates the
- * products in double-float (two float32 words), which the fully constrained
- * solve needs to reach 1e-4 on ill-conditioned libraries. */
-enum { LINMIN_PROJ_DF = 0 };
+/* Projection precision (c = S W^2 y).
+ *   LINMIN_PROJ_DF    double-float (two float32 words) on the CUDA cores;
+ *   LINMIN_PROJ_TC    (default) tensor cores (tcgen05), exact: 8-bit integer slices
+ *                     of y and of W^2 S / s in bf16, float32 accumulation
+ *                     that stays exact, levels combined in double-float
+ *                     (the accuracy of LINMIN_PROJ_DF);
+ *   LINMIN_PROJ_BF16  tensor cores, bf16 y and W^2 S / s, float32
+ *                     accumulation (fast, but c carries bf16 rounding: on
+ *                     ill-conditioned libraries x moves by up to ~1e-2).
+ * The fully constrained solve needs ~1e-11 relative in c to reach 1e-4 in
+ * x on ill-conditioned libraries, hence the exact modes. */
+enum { LINMIN_PROJ_DF = 0, LINMIN_PROJ_TC = 1, LINMIN_PROJ_BF16 = 2 };
 
 /* Constraint set.  LINMIN_STO: x >= 0 and sum x = 1 (Sec. 2.2, FCLS). */
 enum { LINMIN_STO = 0 };
@@ -89,7 +97,7 @@ enum { LINMIN_STO = 0 };
 #define LINMIN_MAX_L 4096
 
 typedef struct {
-    int precision;        /* LINMIN_PROJ_DF */
+    int precision;        /* LINMIN_PROJ_TC (default), _DF or _BF16 */
     int constraint;       /* LINMIN_STO */
     int max_iter;         /* interior-point iteration cap per pixel (default 100) */
     float tol;            /* retry path: complementarity tolerance, each

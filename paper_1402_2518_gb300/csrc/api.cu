@@ -67,6 +67,9 @@ struct linmin_ctx {
     // T = C^-1 S^T scratch, and the hash of the C^-1 last checked
     double *cov = nullptr, *covT = nullptr;
     unsigned long long cov_hash = 0;
+    // tensor-core projection: slices of B~ and column exponents
+    __nv_bfloat16 *bsl = nullptr;
+    int *fexp = nullptr;
     cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
 };
 
@@ -218,6 +221,8 @@ size_t handle_bytes(int L, int P, long long N, bool host_io)
     size_t fixed = 4 * (size_t)P * L + 8 * 2 * (size_t)P * P + 8 + 4 * 2 * PPM * PPM + 4 * PPM +
                    4 * (size_t)P + 4 * 2 * (size_t)L * PQ + 4 + 8 * 8 +
                    8 * (MAX_SWAPS + 2) + 8 + 8 * ((size_t)P + 1) + 4 * ((size_t)P + 1);
+    // tensor-core projection (the default precision): T, slices, exponents
+    fixed += 8 * (size_t)L * P + tc_bslice_bytes(L, P, LINMIN_PROJ_TC) + 4 * (size_t)P;
     size_t per_pixel = 4 * 4 * (size_t)P + 4 + 4 + 8 + 8 + 8 + 8 + 4;
     if (host_io) per_pixel += 4 * (size_t)L + 2 * 4 * (size_t)P + 4 + 4;
     return fixed + (host_io ? 4 * (size_t)L : 0) + per_pixel * n;
@@ -232,7 +237,7 @@ const char *linmin_version(void) { return "linmin-gb300 0.1 (sm_103a)"; }
 linmin_status linmin_default_options(linmin_options *opt)
 {
     if (!opt) return LINMIN_ERR_INVALID;
-    opt->precision = LINMIN_PROJ_DF;
+    opt->precision = LINMIN_PROJ_TC;
     opt->constraint = LINMIN_STO;
     opt->max_iter = 100;
     opt->tol = 1e-9f;
@@ -255,8 +260,10 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     linmin_options o;
     linmin_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != LINMIN_PROJ_DF || o.constraint != LINMIN_STO)
-        return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "only PROJ_DF and STO are built");
+    if ((o.precision != LINMIN_PROJ_DF && o.precision != LINMIN_PROJ_TC &&
+         o.precision != LINMIN_PROJ_BF16) || o.constraint != LINMIN_STO)
+        return fail(nullptr, LINMIN_ERR_UNSUPPORTED,
+                    "precision must be PROJ_DF, PROJ_TC or PROJ_BF16; constraint STO");
     if (o.max_iter < 1 || !(o.tol > 0.f) || !(o.refine_mu > 0.f))
         return fail(nullptr, LINMIN_ERR_INVALID, "max_iter >= 1, tol > 0, refine_mu > 0");
 
@@ -369,8 +376,8 @@ static linmin_status load_cov(linmin_ctx *h, const double *cov_inv)
     cudaError_t a = cudaSuccess;
     if (!h->cov) {
         a = dalloc(h, &h->cov, n);
-        if (a == cudaSuccess) a = dalloc(h, &h->covT, (size_t)L * h->P);
-        if (a != cudaSuccess) { h->cov = h->covT = nullptr; return cuda_fail(h, a, "cov allocation"); }
+        if (a == cudaSuccess && !h->covT) a = dalloc(h, &h->covT, (size_t)L * h->P);
+        if (a != cudaSuccess) return cuda_fail(h, a, "cov allocation");
     }
     LM_CUDA(h, cudaMemcpyAsync(h->cov, sym.data(), n * 8, cudaMemcpyHostToDevice, h->stream),
             "upload cov_inv");
@@ -438,8 +445,21 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     else
         LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
     mark(h, 1);
-    LM_CUDA(h, launch_project(d_cube, N, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st),
-            "projection kernel");
+    int proj_launches = 1;
+    if (h->opt.precision == LINMIN_PROJ_DF) {
+        LM_CUDA(h, launch_project(d_cube, N, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st),
+                "projection kernel");
+    } else {
+        if (!cov_inv) {
+            LM_CUDA(h, launch_prep_t_diag(h->dS, d_sigma, L, P, h->covT, st), "projection prep");
+            ++proj_launches;
+        }
+        LM_CUDA(h, launch_tc_prep(h->covT, L, P, h->prep.scale, h->opt.precision, h->bsl, h->fexp,
+                                  st), "projection prep");
+        proj_launches += h->opt.precision == LINMIN_PROJ_TC ? 2 : 1;
+        LM_CUDA(h, launch_project_tc(d_cube, N, L, P, h->opt.precision, h->bsl, h->fexp, h->c_hi,
+                                     h->c_lo, h->prep.flags, st), "tensor-core projection");
+    }
     mark(h, 2);
 
     IpmArgs ia = ipm_args(h, N);
@@ -470,7 +490,8 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
     if (h->opt.profile) ++h->calls;
-    h->launches = (cov_inv ? PREP_COV_LAUNCHES : PREP_LAUNCHES) + 1 + 1 + crossover_launches(true) +
+    h->launches = (cov_inv ? PREP_COV_LAUNCHES : PREP_LAUNCHES) + proj_launches + 1 +
+                  crossover_launches(true) +
                   2 + crossover_launches(false) + (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
                       "copy iterations");
@@ -518,6 +539,7 @@ linmin_status linmin_wait(linmin_handle h, long long *n_not_converged)
     if (n_not_converged) *n_not_converged = (long long)c[2];
     if (flags & 1) return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
     if (flags & 2) return fail(h, LINMIN_ERR_INVALID, "library has a zero whitened scale");
+    if (flags & 4) return fail(h, LINMIN_ERR_TIMEOUT, "tensor-core projection: an MMA did not complete");
     if (c[2]) return fail(h, LINMIN_ERR_NOT_CONVERGED,
                           std::to_string(c[2]) + " pixels hit max_iter");
     return LINMIN_OK;
@@ -686,6 +708,11 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
     A(dalloc(h, &h->xw.len_all, 1));
     A(dalloc(h, &h->xw.cursor, (size_t)P + 1));
     A(dalloc(h, &h->xw.hist, (size_t)P + 1));
+    if (o.precision != LINMIN_PROJ_DF) {
+        A(dalloc(h, &h->covT, (size_t)L * P));
+        A(dalloc(h, &h->bsl, tc_bslice_bytes(L, P, o.precision) / 2));
+        A(dalloc(h, &h->fexp, (size_t)P));
+    }
     A(cudaMemcpyAsync(h->dS, hS, (size_t)P * L * 4, cudaMemcpyHostToDevice, h->stream));
     A(cudaStreamSynchronize(h->stream));       // hS belongs to the caller
     if (o.profile)
@@ -714,7 +741,8 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
                     h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
                     h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
-                    h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT};
+                    h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT, h->bsl,
+                    h->fexp};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     if (h->pool) pool_release(h->device);

@@ -1,5 +1,6 @@
 // Launch interfaces between the C ABI (api.cu) and the kernels.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -49,6 +50,18 @@ cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP
 // Full noise covariance: C^-1 (L x L fp64, device), T scratch (L x P fp64).
 cudaError_t launch_prep_cov(const float *S, const double *Cinv, int L, int P, int PP,
                             const Prep &o, double *T, cudaStream_t st);
+// Tensor-core projection (project_tc.cu).  T: W^2 S^T (per band, from
+// launch_prep_t_diag) or C^-1 S^T (full covariance), L x P fp64; mode
+// LINMIN_PROJ_TC or LINMIN_PROJ_BF16; err: bit 2 set when an MMA did not
+// complete within the wait limit.
+cudaError_t launch_prep_t_diag(const float *S, const float *sigma, int L, int P, double *T,
+                               cudaStream_t st);
+size_t tc_bslice_bytes(int L, int P, int mode);
+cudaError_t launch_tc_prep(const double *T, int L, int P, const double *scale, int mode,
+                           __nv_bfloat16 *bsl, int *fexp, cudaStream_t st);
+cudaError_t launch_project_tc(const float *cube, long long N, int L, int P, int mode,
+                              const __nv_bfloat16 *bsl, const int *fexp, float *c_hi,
+                              float *c_lo, int *err, cudaStream_t st);
 cudaError_t launch_project(const float *cube, long long N, int L, int P,
                            const float *Bhi, const float *Blo, float *c_hi,
                            float *c_lo, cudaStream_t st);

@@ -38,6 +38,8 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
+LINMIN_PROJ_TC = 1
+LINMIN_PROJ_BF16 = 2
 PHASES = ("prep", "project", "ipm", "crossover", "retry", "rms")
 
 
@@ -291,7 +293,8 @@ class Unmixer:
     on the device of the inputs (plumbing only)."""
 
     def __init__(self, library, max_iter: int = 100, tol: float = 1e-9,
-                 refine_mu: float = 1e-9, stream=None, profile: bool = False):
+                 refine_mu: float = 1e-9, stream=None, profile: bool = False,
+                 precision: int | None = None):
         import torch
         S = library if hasattr(library, "data_ptr") else torch.as_tensor(library)
         S = S.to(torch.float32).contiguous()
@@ -299,6 +302,8 @@ class Unmixer:
         opt = linmin_default_options()
         opt.max_iter, opt.tol, opt.refine_mu = int(max_iter), float(tol), float(refine_mu)
         opt.profile = int(bool(profile))
+        if precision is not None:
+            opt.precision = int(precision)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(stream.cuda_stream))
         self.h = linmin_create(S, self.L, self.P, opt)

@@ -53,7 +53,7 @@ def test_options_struct_layout_and_defaults():
     o = pkg.linmin_default_options()
     assert ctypes.sizeof(linmin.linmin_options) == 40
     assert o.max_iter == 100 and abs(o.tol - 1e-9) < 1e-15 and abs(o.refine_mu - 1e-9) < 1e-15
-    assert o.precision == linmin.LINMIN_PROJ_DF and o.constraint == linmin.LINMIN_STO
+    assert o.precision == linmin.LINMIN_PROJ_TC and o.constraint == linmin.LINMIN_STO
 
 
 def test_invalid_arguments_rejected_on_host():
