@@ -50,6 +50,7 @@ struct linmin_ctx {
     int *it = nullptr;
     long long *retry = nullptr;
     unsigned long long *mask = nullptr;
+    int *rexp = nullptr;               // per-pixel exponents of the TMA projection
     CrossoverScratch xw{};
     // host-pointer staging
     long long capIO = 0;
@@ -223,7 +224,7 @@ size_t handle_bytes(int L, int P, long long N, bool host_io)
                    8 * (MAX_SWAPS + 2) + 8 + 8 * ((size_t)P + 1) + 4 * ((size_t)P + 1);
     // tensor-core projection (the default precision): T, slices, exponents
     fixed += 8 * (size_t)L * P + tc_bslice_bytes(L, P, LINMIN_PROJ_TC) + 4 * (size_t)P;
-    size_t per_pixel = 4 * 4 * (size_t)P + 4 + 4 + 8 + 8 + 8 + 8 + 4;
+    size_t per_pixel = 4 * 4 * (size_t)P + 4 + 4 + 8 + 8 + 8 + 8 + 4 + 4;
     if (host_io) per_pixel += 4 * (size_t)L + 2 * 4 * (size_t)P + 4 + 4;
     return fixed + (host_io ? 4 * (size_t)L : 0) + per_pixel * n;
 }
@@ -291,6 +292,7 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     A(dalloc(h, &h->xw.list[0], (size_t)N));
     A(dalloc(h, &h->xw.list[1], (size_t)N));
     A(dalloc(h, &h->xw.ksize, (size_t)N));
+    A(dalloc(h, &h->rexp, (size_t)N));
 #undef A
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
@@ -457,8 +459,15 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
         LM_CUDA(h, launch_tc_prep(h->covT, L, P, h->prep.scale, h->opt.precision, h->bsl, h->fexp,
                                   st), "projection prep");
         proj_launches += h->opt.precision == LINMIN_PROJ_TC ? 2 : 1;
-        LM_CUDA(h, launch_project_tc(d_cube, N, L, P, h->opt.precision, h->bsl, h->fexp, h->c_hi,
-                                     h->c_lo, h->prep.flags, st), "tensor-core projection");
+        if (h->opt.precision == LINMIN_PROJ_TC && tc2_usable(d_cube, N, L)) {
+            LM_CUDA(h, launch_project_tc2(d_cube, N, L, P, h->bsl, h->fexp, h->rexp, h->c_hi,
+                                          h->c_lo, h->prep.flags, st), "tensor-core projection");
+            ++proj_launches;
+        } else {
+            LM_CUDA(h, launch_project_tc(d_cube, N, L, P, h->opt.precision, h->bsl, h->fexp,
+                                         h->c_hi, h->c_lo, h->prep.flags, st),
+                    "tensor-core projection");
+        }
     }
     mark(h, 2);
 
@@ -738,7 +747,7 @@ linmin_status lm::destroy_async(linmin_handle h)
             if (e) cudaEventDestroy(e);
     void *ptrs[] = {h->dS, h->prep.G64, h->prep.Gt64, h->prep.scale, h->prep.Ghi, h->prep.Glo,
                     h->prep.grs, h->prep.gdiag, h->prep.Bhi, h->prep.Blo, h->prep.flags, h->dcnt,
-                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask,
+                    h->c_hi, h->c_lo, h->x, h->lam, h->nu, h->it, h->retry, h->mask, h->rexp,
                     h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
                     h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
                     h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT, h->bsl,

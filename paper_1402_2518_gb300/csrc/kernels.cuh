@@ -62,6 +62,13 @@ cudaError_t launch_tc_prep(const double *T, int L, int P, const double *scale, i
 cudaError_t launch_project_tc(const float *cube, long long N, int L, int P, int mode,
                               const __nv_bfloat16 *bsl, const int *fexp, float *c_hi,
                               float *c_lo, int *err, cudaStream_t st);
+// TMA-fed exact projection (per-pixel exponent pass into rexp, N ints,
+// then the pipelined GEMM): usable when rows are 16-byte strided and
+// aligned; otherwise launch_project_tc.
+bool tc2_usable(const float *cube, long long N, int L);
+cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
+                               const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
+                               float *c_lo, int *err, cudaStream_t st);
 cudaError_t launch_project(const float *cube, long long N, int L, int P,
                            const float *Bhi, const float *Blo, float *c_hi,
                            float *c_lo, cudaStream_t st);

@@ -7,14 +7,14 @@
 // up to 1e-2), far beyond bf16 or tf32 inputs with float32 accumulation.
 //
 // Exact mode (LINMIN_PROJ_TC): every pixel row is scaled by a power of two
-// so that |y_l| < 1 and cut into NS integer slices of 8 bits each,
-//     y_l 2^-e = sum_i a_il 2^-8(i+1),   a_0 in [-256, 256], a_i>0 in [-128, 128]
+// so that |y_l| < 1/2 and cut into NS integer slices of 8 bits each,
+//     y_l 2^-e = sum_i a_il 2^-8(i+1),   a_i in [-128, 128]
 // (round-to-nearest residues, exact in float32), and every column of B~
 // likewise (exponent f_j, slices b_qlj).  The integers are exact in bf16;
-// the products a b are exact in float32 and, summed over at most 128 bands
-// and the <= 5 slice pairs of one level l = i + q, stay below 2^24, so the
-// tensor core's float32 accumulation is exact too.  The 15 slice pairs with
-// i + q <= 4 accumulate into 5 TMEM accumulators (one per level); every 128
+// the products a b (<= 2^14) are exact in float32 and, summed over at most
+// 192 bands and the <= 5 slice pairs of one level l = i + q, stay below
+// 2^24, so the tensor core's float32 accumulation is exact too.  The 15 slice pairs with
+// i + q <= 4 accumulate into 5 TMEM accumulators (one per level); every 192
 // bands each thread adds them, weighted 2^-8(l+2), to double-float sums,
 // and c_j = 2^(e + f_j) sum + rho.  Dropped terms (the slice residues and
 // the levels above 4) are below 2^-39 of max|y| max|B_j| per band: the
@@ -32,9 +32,12 @@
 // layout) to shared memory, one thread issues the MMAs (M = 128, N = P
 // padded to 16, K = 16), tcgen05.commit signals an mbarrier, and the
 // epilogue reads the accumulators with tcgen05.ld.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -47,7 +50,7 @@ namespace {
 constexpr int TC_M = 128;           // pixels per tile = MMA M = TMEM lanes
 constexpr int TC_KC = 64;           // bands per chunk
 constexpr int TC_THREADS = 256;     // 8 warps
-constexpr int TC_GROUP = 2;         // chunks per exact accumulation group (128 bands)
+constexpr int TC_GROUP = 3;         // chunks per exact accumulation group (192 bands)
 // TMEM columns a CTA allocates: a power of two >= the NL * NPAD accumulators
 __host__ __device__ constexpr int tc_tmem_cols(int need) { return need <= 256 ? 256 : 512; }
 constexpr long long WAIT_LIMIT = 1LL << 26;   // bounded mbarrier wait (error flag)
@@ -137,6 +140,27 @@ __device__ __forceinline__ uint4 pack8(const float (&v)[8])
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// 2^k as a float for -126 <= k <= 127
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+// x 2^-e exactly (two power-of-two factors keep both in the normal range)
+__device__ __forceinline__ float scale_pow2(float x, int e)
+{
+    const int h = e / 2;
+    return x * pow2f(-h) * pow2f(h - e);
+}
+
+// df accumulate of a value whose magnitude is close to the total's
+__device__ __forceinline__ df df_add_near(df a, float bh, float bl)
+{
+    float s, e;
+    two_sum(a.hi, bh, s, e);
+    e += a.lo + bl;
+    df r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
 // exact slice count and levels of a mode
 template <int MODE> struct TcMode;
 template <> struct TcMode<LINMIN_PROJ_TC> { static constexpr int NS = 5, NL = 5; };
@@ -157,7 +181,7 @@ __global__ void tc_bexp_kernel(const double *__restrict__ T, int L, int P,
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
     if (lane == 0) {
         int e = 0;
-        if (m > 0.0) frexp(m, &e);
+        if (m > 0.0) { frexp(m, &e); ++e; }          // |B~_lj| 2^-f_j < 1/2
         fexp[j] = e;
     }
 }
@@ -183,7 +207,7 @@ __global__ void tc_bslice_kernel(const double *__restrict__ T, int L, int P, int
         if (MODE == LINMIN_PROJ_BF16) {
             *reinterpret_cast<__nv_bfloat16 *>(blk + kmaj(j, k, NPAD)) = __double2bfloat16(v);
         } else {
-            double r = j < P ? ldexp(v, -fexp[j]) : 0.0;     // |r| < 1, exact scaling
+            double r = j < P ? ldexp(v, -fexp[j]) : 0.0;     // |r| < 1/2, exact scaling
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 const double t = r * 256.0;
@@ -270,7 +294,7 @@ project_tc_kernel(const float *__restrict__ cube, long long N, int L, int P,
             for (int i = tid; i < TC_M; i += TC_THREADS) {
                 const float m = __int_as_float(pexp[i]);
                 int e = 0;
-                if (m > 0.f) frexpf(m, &e);
+                if (m > 0.f) { frexpf(m, &e); ++e; }     // |y_l| 2^-e < 1/2
                 pexp[i] = e;
             }
         }
@@ -312,8 +336,10 @@ project_tc_kernel(const float *__restrict__ cube, long long N, int L, int P,
                 } else {
                     const int e = pexp[pix];
                     float r[8];
+                    const int h = e / 2;
+                    const float f1 = pow2f(-h), f2 = pow2f(h - e);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) r[q] = ldexpf(yv[u][q], -e);   // exact
+                    for (int q = 0; q < 8; ++q) r[q] = yv[u][q] * f1 * f2;       // exact
 #pragma unroll
                     for (int i = 0; i < NS; ++i) {
                         float a[8];
@@ -419,6 +445,353 @@ project_tc_kernel(const float *__restrict__ cube, long long N, int L, int P,
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
                      :: "r"(tmem), "r"(TMEM_COLS));
+}
+
+// --------------------------------------------------- TMA-fed exact GEMM
+// Per-pixel exponents (max_l |y_l| < 2^e) in one coalesced pass: warp per row.
+__global__ void tc_rowexp_kernel(const float *__restrict__ cube, long long N, int L,
+                                 int *__restrict__ rexp)
+{
+    const long long n = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (n >= N) return;
+    const float *y = cube + (size_t)n * L;
+    float m = 0.f;
+    for (int l = lane; l < L; l += 32) m = fmaxf(m, fabsf(__ldg(y + l)));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) {
+        int e = 0;
+        if (m > 0.f) { frexpf(m, &e); ++e; }         // |y_l| 2^-e < 1/2
+        rexp[n] = e;
+    }
+}
+
+constexpr int TC2_THREADS = 512;    // 16 warps, one CTA per SM
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+                 " [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t addr, float (&v)[4])
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Exact projection with the chunks of every tile double-buffered: while
+// chunk g is sliced and multiplied, the tensor map copies the pixel tile of
+// chunk g + 1 (128 pixels x 64 bands, zero past N and L) and a bulk copy
+// brings its B~ slices, both completing on that buffer's mbarrier.
+template <int NPAD>
+__global__ void __launch_bounds__(TC2_THREADS, 1)
+project_tc2_kernel(const __grid_constant__ CUtensorMap ymap, long long N, int L, int P,
+                   const __nv_bfloat16 *__restrict__ bsl, const int *__restrict__ fexp,
+                   const int *__restrict__ rexp, float *__restrict__ c_hi,
+                   float *__restrict__ c_lo, int *__restrict__ err)
+{
+    constexpr int NS = TcMode<LINMIN_PROJ_TC>::NS, NL = TcMode<LINMIN_PROJ_TC>::NL;
+    constexpr int Y_TILE = TC_M * TC_KC * 4;          // fp32 pixel tile of a chunk
+    constexpr int A_SLICE = TC_M * TC_KC * 2;
+    constexpr int B_SLICE = NPAD * TC_KC * 2;
+    constexpr int QCOL = NPAD / 4;                    // columns per epilogue warp
+    constexpr int TMEM_COLS = tc_tmem_cols(NL * NPAD);
+    static_assert(QCOL % 4 == 0, "epilogue loads 4 columns at a time");
+    static_assert(TC_M * (TC_KC / 8) % TC2_THREADS == 0, "slicing items per thread");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sY = smem;                          // 2 pixel tiles
+    unsigned char *sA = smem + 2 * Y_TILE;             // NS pixel slices
+    unsigned char *sB = sA + NS * A_SLICE;             // 2 x NS B~ slices
+    __shared__ __align__(8) uint64_t bar_load[2];
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t tbase;
+    __shared__ int pexp[2][TC_M];                      // exponents of the tile (by parity)
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nchunks = (L + TC_KC - 1) / TC_KC;
+    const long long ntiles = (N + TC_M - 1) / TC_M;
+    const long long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long nwork = my_tiles * nchunks;        // chunks this CTA runs
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&bar_load[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&bar_load[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&bar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(su32(&tbase)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tbase;
+
+    // chunk g of this CTA: tile blockIdx.x + (g / nchunks) * gridDim.x, chunk g % nchunks
+    auto issue = [&](long long g) {
+        const long long t = blockIdx.x + (g / nchunks) * gridDim.x;
+        const int c = (int)(g % nchunks), b = (int)(g & 1);
+        const uint32_t bar = su32(&bar_load[b]);
+        mbar_expect_tx(bar, (uint32_t)(Y_TILE + NS * B_SLICE));
+        tma_load_2d(su32(sY + b * Y_TILE), &ymap, c * TC_KC, (int)(t * TC_M), bar);
+        bulk_load(su32(sB + b * NS * B_SLICE),
+                  reinterpret_cast<const char *>(bsl) + (size_t)c * NS * B_SLICE,
+                  (uint32_t)(NS * B_SLICE), bar);
+    };
+
+    // epilogue role: TMEM lanes of warp (warp & 3), columns of quarter (warp >> 2)
+    const int ep_pix = 32 * (warp & 3) + lane;
+    const int ep_col0 = QCOL * (warp >> 2);
+    df acc[QCOL];
+#pragma unroll
+    for (int j = 0; j < QCOL; ++j) acc[j] = df_make(0.f);
+
+    bool ok = true;
+    uint32_t mma_phase = 0;
+    if (tid == 0 && nwork > 0) issue(0);
+    for (long long g = 0; g <= nwork && ok; ++g) {
+        // 1. the MMAs of chunk g - 1 are complete: fold at a group end, write
+        //    at a tile end
+        if (g > 0) {
+            ok = __syncthreads_and(mbar_wait(su32(&bar_mma), mma_phase));
+            mma_phase ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!ok) break;
+            const int cp = (int)((g - 1) % nchunks);
+            const long long tp = blockIdx.x + ((g - 1) / nchunks) * gridDim.x;
+            if ((cp % TC_GROUP) == TC_GROUP - 1 || cp == nchunks - 1) {
+#pragma unroll
+                for (int j4 = 0; j4 < QCOL / 4; ++j4) {
+                    float sh[4], sl[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
+#pragma unroll
+                    for (int lv = NL - 1; lv >= 0; --lv) {
+                        float v[4];
+                        tmem_ld4(tmem + ((uint32_t)(32 * (warp & 3)) << 16) +
+                                     (uint32_t)(lv * NPAD + ep_col0 + 4 * j4), v);
+                        const float w = pow2f(-8 * (lv + 2));
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float t, e;
+                            two_sum(sh[q], v[q] * w, t, e);
+                            sh[q] = t;
+                            sl[q] += e;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        acc[4 * j4 + q] = df_add_near(acc[4 * j4 + q], sh[q], sl[q]);
+                }
+                if (cp == nchunks - 1) {
+                    const long long n = tp * TC_M + ep_pix;
+                    if (n < N) {
+                        const int e = pexp[(int)(((g - 1) / nchunks) & 1)][ep_pix];
+#pragma unroll
+                        for (int j = 0; j < QCOL; ++j) {
+                            const int col = ep_col0 + j;
+                            if (col < P) {
+                                const int sh2 = e + fexp[col];
+                                df v = df{ldexpf(acc[j].hi, sh2), ldexpf(acc[j].lo, sh2)};
+                                v = df_add(v, df_make((float)RHO));
+                                c_hi[(size_t)n * P + col] = v.hi;
+                                c_lo[(size_t)n * P + col] = v.lo;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < QCOL; ++j) acc[j] = df_make(0.f);
+                }
+            }
+        }
+        if (g == nwork) break;
+        const int c = (int)(g % nchunks), b = (int)(g & 1);
+        const long long t = blockIdx.x + (g / nchunks) * gridDim.x;
+        if (c == 0)
+            for (int i = tid; i < TC_M; i += TC_THREADS) {
+                const long long n = t * TC_M + i;
+                pexp[(int)((g / nchunks) & 1)][i] = n < N ? rexp[n] : 0;
+            }
+        // 2. TMEM read and buffer (g + 1) & 1 (last used by chunk g - 1) free
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0 && g + 1 < nwork) issue(g + 1);
+        // 3. chunk g's pixel tile and B~ slices have landed
+        ok = __syncthreads_and(mbar_wait(su32(&bar_load[b]), (uint32_t)((g >> 1) & 1)));
+        if (!ok) break;
+        // 4. pixel slices from the tile (row-major, 64 bands of 4 bytes)
+        const int* pe = pexp[(int)((g / nchunks) & 1)];
+#pragma unroll
+        for (int u = 0; u < TC_M * (TC_KC / 8) / TC2_THREADS; ++u) {
+            const int it = tid + u * TC2_THREADS;
+            const int pix = it % TC_M, oct = it / TC_M;
+            const float4 *row = reinterpret_cast<const float4 *>(sY + b * Y_TILE + pix * TC_KC * 4 +
+                                                                 oct * 32);
+            const float4 v0 = row[0], v1 = row[1];
+            const int e = pe[pix];
+            float r[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            const int h = e / 2;
+            const float f1 = pow2f(-h), f2 = pow2f(h - e);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) r[q] = r[q] * f1 * f2;          // exact
+            const int off = kmaj(pix, 8 * oct, TC_M);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                float a[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float tt = r[q] * 256.f;
+                    a[q] = rintf(tt);
+                    r[q] = tt - a[q];
+                }
+                *reinterpret_cast<uint4 *>(sA + i * A_SLICE + off) = pack8(a);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // 5. the MMAs of chunk g
+        if (tid == 0) {
+            constexpr uint32_t ID = idesc_bf16(TC_M, NPAD);
+            constexpr uint32_t LBO_A = (TC_M / 8) * 128, LBO_B = (NPAD / 8) * 128;
+            const bool first = (c % TC_GROUP) == 0;
+            // descriptors are affine in the start address (its 16-byte units
+            // are the low bits): bases once, compile-time offsets per MMA
+            const uint64_t a0 = sdesc(su32(sA), LBO_A, 128);
+            const uint64_t b0 = sdesc(su32(sB + b * NS * B_SLICE), LBO_B, 128);
+#pragma unroll
+            for (int lv = 0; lv < NL; ++lv) {
+                bool fresh = first;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) {
+                    const int q = lv - i;
+                    if (q < 0 || q >= NS) continue;
+#pragma unroll
+                    for (int kk = 0; kk < TC_KC / 16; ++kk) {
+                        const uint64_t ad = a0 + (uint64_t)((i * A_SLICE + kk * 2 * LBO_A) >> 4);
+                        const uint64_t bd = b0 + (uint64_t)((q * B_SLICE + kk * 2 * LBO_B) >> 4);
+                        mma_bf16(tmem + (uint32_t)(lv * NPAD), ad, bd, ID, fresh ? 0u : 1u);
+                        fresh = false;
+                    }
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(su32(&bar_mma)));
+        }
+    }
+    if (!ok) {
+        // flag, then give copies and MMAs in flight a second bounded wait
+        if (tid == 0) atomicOr(err, 4);
+        mbar_wait(su32(&bar_mma), mma_phase);
+        mbar_wait(su32(&bar_load[0]), 0);
+        mbar_wait(su32(&bar_load[1]), 0);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"(TMEM_COLS));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// the TMA path applies when rows are 16-byte strided and aligned
+bool tc2_usable(const float *cube, long long N, int L)
+{
+    return (L % 4) == 0 && (reinterpret_cast<uintptr_t>(cube) % 16) == 0 && N < (1LL << 31) &&
+           encode_tiled() != nullptr;
+}
+
+template <int NPAD>
+static cudaError_t launch_tc2_t(const float *cube, long long N, int L, int P,
+                                const __nv_bfloat16 *bsl, const int *fexp, const int *rexp,
+                                float *c_hi, float *c_lo, int *err, cudaStream_t st)
+{
+    constexpr int NS = TcMode<LINMIN_PROJ_TC>::NS;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)N};
+    const cuuint64_t strides[1] = {(cuuint64_t)L * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)TC_KC, (cuuint32_t)TC_M};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode_tiled()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(cube), dims,
+                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    const size_t smem = 2 * (size_t)TC_M * TC_KC * 4 + (size_t)NS * TC_M * TC_KC * 2 +
+                        2 * (size_t)NS * NPAD * TC_KC * 2;
+    cudaError_t e = cudaFuncSetAttribute(project_tc2_kernel<NPAD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_rowexp_kernel<<<(unsigned)((N * 32 + 255) / 256), 256, 0, st>>>(cube, N, L,
+                                                                      const_cast<int *>(rexp));
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long ntiles = (N + TC_M - 1) / TC_M;
+    const unsigned blocks = (unsigned)(ntiles < sms ? ntiles : sms);
+    project_tc2_kernel<NPAD><<<blocks, TC2_THREADS, smem, st>>>(map, N, L, P, bsl, fexp, rexp,
+                                                                c_hi, c_lo, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
+                               const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
+                               float *c_lo, int *err, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    switch (((P + 15) / 16) * 16) {
+    case 16: return launch_tc2_t<16>(cube, N, L, P, bsl, fexp, rexp, c_hi, c_lo, err, st);
+    case 32: return launch_tc2_t<32>(cube, N, L, P, bsl, fexp, rexp, c_hi, c_lo, err, st);
+    case 48: return launch_tc2_t<48>(cube, N, L, P, bsl, fexp, rexp, c_hi, c_lo, err, st);
+    case 64: return launch_tc2_t<64>(cube, N, L, P, bsl, fexp, rexp, c_hi, c_lo, err, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 // ------------------------------------------------------------------ launch

@@ -140,8 +140,9 @@ def test_server_handle_bytes():
     b2 = pkg.linmin_server_handle_bytes(184, 36, 2000)
     bh = pkg.linmin_server_handle_bytes(184, 36, 1000, host_io=True)
     # per pixel: c~ hi/lo, x, lambda (4 P floats) + nu, iterations, retry,
-    # mask, two lists, support size (44 bytes); staging adds cube + outputs
-    assert b2 - b == 1000 * (16 * 36 + 44)
+    # mask, two lists, support size, pixel exponent (48 bytes); staging adds
+    # cube + outputs
+    assert b2 - b == 1000 * (16 * 36 + 48)
     assert bh - b == 1000 * (4 * 184 + 8 * 36 + 8) + 4 * 184
     assert pkg.linmin_server_handle_bytes(184, 65, 10) == 0
 
