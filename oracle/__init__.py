@@ -185,6 +185,47 @@ def unmix(S, sigma, X, nthreads: int = 0, max_iter: int = MAX_ITER,
     return out
 
 
+POS_SCALE = 4096.0
+
+
+def unmix_constraint(S, sigma, X, constraint: str = "sto", max_iter: int = MAX_ITER):
+    """Unmixing under the constraint sets of the paper (Sec. 2.2): "sto"
+    x >= 0, sum x = 1 (``unmix``); "slo" x >= 0, sum x <= 1; "pos" x >= 0.
+
+    slo is the sum-to-one problem on the library with a zero spectrum
+    appended: its coefficient w = 1 - sum x >= 0 is the slack of the
+    inequality and adds nothing to the fit, so the two problems have the
+    same minimiser.  pos is slo on POS_SCALE S (x = POS_SCALE x'), the same
+    as pos whenever sum x < POS_SCALE (pixels where the bound is reached get
+    negative iteration counts).  The uncertainty is the support-restricted
+    one of ``unmix``: with the slack in the support the sum is free.
+
+    Returns dict(x, sx, rms, iters, lam, slack) like ``unmix``."""
+    if constraint == "sto":
+        return unmix(S, sigma, X, max_iter=max_iter)
+    if constraint not in ("slo", "pos"):
+        raise ValueError("constraint must be sto, slo or pos")
+    M = POS_SCALE if constraint == "pos" else 1.0
+    S32 = _f32(S)
+    P, L = S32.shape
+    Sa = np.vstack([S32.astype(np.float64) * M, np.zeros((1, L))]).astype(np.float32)
+    r = unmix(Sa, sigma, X, max_iter=max_iter)
+    # support: lambda_i < x_i G_ii, with unit curvature for the slack (its
+    # spectrum is zero, G_ww = 0); the uncertainty on that support
+    G, _ = prep(Sa, sigma)
+    sx = np.empty_like(r["sx"])
+    for n in range(r["x"].shape[0]):
+        m = support(G, r["x"][n], r["lam"][n])
+        m[P] = r["lam"][n][P] < r["x"][n][P]
+        sx[n] = sigma_x(G, m)
+    out = dict(x=r["x"][:, :P] * M, sx=sx[:, :P] * M, rms=r["rms"],
+               iters=r["iters"].copy(), lam=r["lam"][:, :P], slack=r["x"][:, P] * M)
+    if constraint == "pos":
+        bound = r["x"][:, P] <= 0.0
+        out["iters"][bound] = -np.abs(out["iters"][bound]) - 1
+    return out
+
+
 def unmix_cov(S, cov_inv, X, max_iter: int = MAX_ITER):
     """Unmixing under a full noise covariance C (Sec. 2.3, eq.
     RenormalizedProblem: the data are whitened as X' = X L with

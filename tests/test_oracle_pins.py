@@ -308,3 +308,99 @@ def test_cov_monte_carlo_sigma():
     emp = r["x"].std(axis=0, ddof=1)
     pred = r["sx"].mean(axis=0)
     np.testing.assert_allclose(emp, pred, rtol=0.05)
+
+
+# ------------------------------------------- slo and pos constraint sets
+def _full_rank_instance(seed, N, L, P):
+    """Minerals only (no level/slope extras): rank S = P, so that the slo
+    and pos minimisers are unique."""
+    cube = synth.random_instance(seed, N, L, P, n_extras=0)
+    assert np.linalg.matrix_rank(cube.S.astype(np.float64)) == P
+    return cube
+
+
+def test_pos_matches_scipy_nnls():
+    """pos is non-negative least squares on the whitened data (scipy)."""
+    from scipy.optimize import nnls
+    cube = _full_rank_instance(61, 60, 50, 8)
+    r = oracle.unmix_constraint(cube.S, cube.sigma, cube.X, "pos")
+    assert np.all(r["iters"] > 0)
+    w = 1.0 / cube.sigma.astype(np.float64)
+    A = (cube.S.astype(np.float64) * w).T
+    for n in range(cube.N):
+        x, _ = nnls(A, cube.X[n].astype(np.float64) * w, maxiter=5000)
+        assert np.abs(x - r["x"][n]).max() <= 1e-6 * max(1.0, x.max())
+
+
+def test_slo_is_pos_or_sto():
+    """slo equals pos where sum x_pos <= 1 and the sum-to-one minimiser
+    where sum x_pos > 1 (the inequality is then active); both cases occur."""
+    cube = _full_rank_instance(62, 80, 50, 8)
+    X = cube.X.astype(np.float64)
+    X[::2] *= 1.3                                   # brighter pixels: sum > 1
+    X = X.astype(np.float32)
+    slo = oracle.unmix_constraint(cube.S, cube.sigma, X, "slo")
+    pos = oracle.unmix_constraint(cube.S, cube.sigma, X, "pos")
+    sto = oracle.unmix(cube.S, cube.sigma, X)
+    tot = pos["x"].sum(1)
+    below, above = tot < 1 - 1e-6, tot > 1 + 1e-6
+    assert below.sum() > 5 and above.sum() > 5
+    np.testing.assert_allclose(slo["x"][below], pos["x"][below], atol=1e-7)
+    np.testing.assert_allclose(slo["x"][above], sto["x"][above], atol=1e-7)
+    assert np.all(slo["x"].sum(1) <= 1 + 1e-9)
+    # uncertainties: the sum is free where the inequality is inactive (pos),
+    # bordered where it is active (sto)
+    np.testing.assert_allclose(slo["sx"][below], pos["sx"][below], rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(slo["sx"][above], sto["sx"][above], rtol=1e-5, atol=1e-9)
+
+
+def test_slo_brute_force_supports():
+    """Tiny problems: every support with the sum constraint active or not,
+    the feasible candidates' best objective equals the oracle's."""
+    import itertools
+    cube = _full_rank_instance(63, 12, 30, 5)
+    X = (cube.X.astype(np.float64) * np.linspace(0.7, 1.4, cube.N)[:, None]).astype(np.float32)
+    r = oracle.unmix_constraint(cube.S, cube.sigma, X, "slo")
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    P = cube.P
+    for n in range(cube.N):
+        c = B @ X[n].astype(np.float64)
+        best, xb = np.inf, None
+        for k in range(1, P + 1):
+            for S_ in itertools.combinations(range(P), k):
+                idx = list(S_)
+                Gs, cs = G[np.ix_(idx, idx)], c[idx]
+                cands = [np.linalg.solve(Gs, cs)]
+                K = np.block([[Gs, np.ones((k, 1))], [np.ones((1, k)), np.zeros((1, 1))]])
+                cands.append(np.linalg.solve(K, np.concatenate([cs, [1.0]]))[:k])
+                for xs in cands:
+                    if xs.min() < -1e-12 or xs.sum() > 1 + 1e-12:
+                        continue
+                    x = np.zeros(P); x[idx] = xs
+                    f = 0.5 * x @ G @ x - c @ x
+                    if f < best:
+                        best, xb = f, x
+        assert np.abs(r["x"][n] - xb).max() <= 1e-7
+
+
+def test_pos_kkt_and_uncertainty():
+    """pos: gradient ~0 on the support, >= 0 off it; the uncertainty is
+    sqrt(diag(G_SS^-1)) on the support (no sum constraint), 0 off it."""
+    cube = _full_rank_instance(64, 30, 60, 10)
+    r = oracle.unmix_constraint(cube.S, cube.sigma, cube.X, "pos")
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    scale = np.max(np.diag(G))
+    for n in range(cube.N):
+        x = r["x"][n]
+        g = G @ x - B @ cube.X[n].astype(np.float64)
+        S_ = x > 1e-9
+        assert np.abs(g[S_]).max() <= 1e-6 * scale
+        if (~S_).any():
+            assert g[~S_].min() >= -1e-6 * scale
+        idx = np.flatnonzero(S_)
+        ratio = r["lam"][n] / np.maximum(x / oracle.POS_SCALE, 1e-300) / (np.diag(G) * oracle.POS_SCALE ** 2)
+        if np.any((ratio > 1e-3) & (ratio < 1e3)):
+            continue                                 # no strict complementarity
+        sx = np.sqrt(np.diag(np.linalg.inv(G[np.ix_(idx, idx)])))
+        np.testing.assert_allclose(r["sx"][n][idx], sx, rtol=1e-6)
+        assert np.all(r["sx"][n][~S_] == 0.0)
