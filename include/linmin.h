@@ -90,15 +90,27 @@ typedef enum {
  * x on ill-conditioned libraries, hence the exact modes. */
 enum { LINMIN_PROJ_DF = 0, LINMIN_PROJ_TC = 1, LINMIN_PROJ_BF16 = 2 };
 
-/* Constraint set.  LINMIN_STO: x >= 0 and sum x = 1 (Sec. 2.2, FCLS). */
-enum { LINMIN_STO = 0 };
+/* Constraint set (Sec. 2.2 and the variants of Sec. 4):
+ *   LINMIN_STO  x >= 0, sum x = 1 (fully constrained, FCLS; default);
+ *   LINMIN_SLO  x >= 0, sum x <= 1;
+ *   LINMIN_POS  x >= 0.
+ * SLO is solved as STO on the library with a zero spectrum appended (its
+ * coefficient is the slack 1 - sum x >= 0 and adds nothing to the fit);
+ * POS as SLO on LINMIN_POS_SCALE * library, exact while sum x is below
+ * LINMIN_POS_SCALE (a pixel that reaches the bound gets a negative
+ * iteration count and counts as not converged).  Both need rank S = P
+ * (LINMIN_ERR_RANK otherwise) and P <= LINMIN_MAX_P - 1.  The
+ * uncertainties are the support-restricted ones: bordered where the sum
+ * constraint binds, free where it does not. */
+enum { LINMIN_STO = 0, LINMIN_SLO = 1, LINMIN_POS = 2 };
+#define LINMIN_POS_SCALE 64
 
 #define LINMIN_MAX_P 64
 #define LINMIN_MAX_L 4096
 
 typedef struct {
     int precision;        /* LINMIN_PROJ_TC (default), _DF or _BF16 */
-    int constraint;       /* LINMIN_STO */
+    int constraint;       /* LINMIN_STO (default), LINMIN_SLO or LINMIN_POS */
     int max_iter;         /* interior-point iteration cap per pixel (default 100) */
     float tol;            /* retry path: complementarity tolerance, each
                              coordinate ends with min(x_i, lambda_i / s) <= tol,

@@ -31,7 +31,13 @@
 using namespace lm;
 
 struct linmin_ctx {
-    int L = 0, P = 0;
+    int L = 0, P = 0;                  // P: spectra of the internal problem
+    // slo / pos: the caller's P is P - 1 (the last internal spectrum is the
+    // zero slack spectrum), results scaled by M (LINMIN_POS_SCALE for pos)
+    int user_P = 0;
+    bool slack = false;
+    float slack_scale = 1.f;
+    float *xa = nullptr, *sxa = nullptr;   // internal x, sx (N x P) of slo / pos
     Bucket bucket{};
     linmin_options opt{};
     cudaStream_t stream = nullptr;
@@ -180,7 +186,9 @@ static bool full_rank(const std::vector<float> &S, int L, int P)
         double nv = 0.0;
         for (double e : v) nv += e * e;
         nv = std::sqrt(nv);
-        if (nv <= 1e-10 * n0) return false;
+        // a float32 library carries its dependencies only to float32
+        // rounding (~1e-7 of a column): below 1e-6 a column is dependent
+        if (nv <= 1e-6 * n0) return false;
         for (int l = 0; l < n; ++l) Q[(size_t)r * n + l] = v[l] / nv;
         ++r;
     }
@@ -262,9 +270,12 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     linmin_default_options(&o);
     if (opt) o = *opt;
     if ((o.precision != LINMIN_PROJ_DF && o.precision != LINMIN_PROJ_TC &&
-         o.precision != LINMIN_PROJ_BF16) || o.constraint != LINMIN_STO)
+         o.precision != LINMIN_PROJ_BF16) ||
+        (o.constraint != LINMIN_STO && o.constraint != LINMIN_SLO && o.constraint != LINMIN_POS))
         return fail(nullptr, LINMIN_ERR_UNSUPPORTED,
-                    "precision must be PROJ_DF, PROJ_TC or PROJ_BF16; constraint STO");
+                    "precision must be PROJ_DF, PROJ_TC or PROJ_BF16; constraint STO, SLO or POS");
+    if (o.constraint != LINMIN_STO && P + 1 > LINMIN_MAX_P)
+        return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "SLO and POS need P <= LINMIN_MAX_P - 1");
     if (o.max_iter < 1 || !(o.tol > 0.f) || !(o.refine_mu > 0.f))
         return fail(nullptr, LINMIN_ERR_INVALID, "max_iter >= 1, tol > 0, refine_mu > 0");
 
@@ -272,7 +283,22 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     std::string why;
     const linmin_status lst = lm::load_library(library, L, P, &hS, &why);
     if (lst != LINMIN_OK) return fail(nullptr, lst, why);
-    return lm::create_from_host(hS.data(), L, P, o, out);
+    if (o.constraint == LINMIN_STO) return lm::create_from_host(hS.data(), L, P, o, out);
+    // slo / pos: M S with a zero spectrum appended; rank [M S, 0; 1, 1] =
+    // P + 1 exactly when rank S = P
+    const float M = o.constraint == LINMIN_POS ? (float)LINMIN_POS_SCALE : 1.f;
+    std::vector<float> hA((size_t)(P + 1) * L, 0.f);
+    for (size_t e = 0; e < (size_t)P * L; ++e) hA[e] = hS[e];
+    if (!full_rank(hA, L, P + 1))          // on S itself: the test is relative to columns
+        return fail(nullptr, LINMIN_ERR_RANK,
+                    "rank S < P: the SLO / POS minimiser is not unique");
+    for (size_t e = 0; e < (size_t)P * L; ++e) hA[e] = M * hS[e];
+    const linmin_status cst = lm::create_from_host(hA.data(), L, P + 1, o, out);
+    if (cst != LINMIN_OK) return cst;
+    (*out)->user_P = P;
+    (*out)->slack = true;
+    (*out)->slack_scale = M;
+    return LINMIN_OK;
 }
 
 static linmin_status ensure_scratch(linmin_ctx *h, long long N)
@@ -293,6 +319,10 @@ static linmin_status ensure_scratch(linmin_ctx *h, long long N)
     A(dalloc(h, &h->xw.list[1], (size_t)N));
     A(dalloc(h, &h->xw.ksize, (size_t)N));
     A(dalloc(h, &h->rexp, (size_t)N));
+    if (h->slack) {
+        A(dalloc(h, &h->xa, np));
+        A(dalloc(h, &h->sxa, np));
+    }
 #undef A
     if (a != cudaSuccess) { h->capN = 0; return cuda_fail(h, a, "scratch allocation"); }
     h->capN = N;
@@ -307,9 +337,12 @@ static IpmArgs ipm_args(linmin_ctx *h, long long N)
     ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
     ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
     ia.n_notconv = h->dcnt + 2;
-    ia.tol_c = h->opt.tol; ia.tol_d = 1e-6f; ia.eta = 0.99f;
+    // pos works on M S, whose coordinates are M times smaller: the absolute
+    // thresholds of the scaled problem shrink with them (mu with M^2)
+    const float m = h->slack_scale;
+    ia.tol_c = h->opt.tol / (m * m); ia.tol_d = 1e-6f / m; ia.eta = 0.99f;
     ia.list = nullptr; ia.list_len = nullptr;
-    ia.mu_ref = MU_STOP; ia.counter = h->dcnt + 0;
+    ia.mu_ref = MU_STOP / (m * m); ia.counter = h->dcnt + 0;
     return ia;
 }
 
@@ -421,7 +454,7 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     if ((s = ensure_scratch(h, N)) != LINMIN_OK) return s;
     if (host_any && (s = ensure_io(h, N)) != LINMIN_OK) return s;
 
-    const size_t np = (size_t)N * P;
+    const size_t np = (size_t)N * h->user_P;    // caller-visible N x P outputs
     const float *d_cube = cube, *d_sigma = sigma;
     if (!dev_cube) {
         LM_CUDA(h, cudaMemcpyAsync(h->io_cube, cube, (size_t)N * L * 4, cudaMemcpyHostToDevice, st),
@@ -435,6 +468,12 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     }
     float *d_x = abundances ? (dev_out[0] ? abundances : h->io_x) : h->x;
     float *d_sx = uncertainties ? (dev_out[1] ? uncertainties : h->io_sx) : nullptr;
+    // slo / pos: the pipeline writes the internal (slack-augmented) results
+    float *u_x = d_x, *u_sx = d_sx;
+    if (h->slack) {
+        d_x = h->xa;
+        d_sx = uncertainties ? h->sxa : nullptr;
+    }
     float *d_rms = residual_rms ? (dev_out[2] ? residual_rms : h->io_rms) : nullptr;
     int *d_it = iterations ? (dev_out[3] ? iterations : h->io_it) : nullptr;
 
@@ -473,7 +512,7 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
 
     IpmArgs ia = ipm_args(h, N);
     // 3. all pixels: float32 residual until mu <= mu_stop
-    ia.mu_ref = MU_STOP; ia.counter = h->dcnt + 0;
+    ia.counter = h->dcnt + 0;
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel");
     mark(h, 3);
     // 4. crossover; failures appended to the retry list
@@ -483,17 +522,20 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     ca.c_hi = h->c_hi; ca.c_lo = h->c_lo; ca.x_in = h->x; ca.lam_in = h->lam;
     ca.x_out = d_x; ca.sx_out = d_sx; ca.mask = h->mask;
     ca.retry_list = h->retry; ca.retry_len = h->dcnt + 5; ca.n_unverified = nullptr;
-    ca.tol_x = 1e-9; ca.tol_g = 1e-9;
+    ca.tol_x = 1e-9 / h->slack_scale; ca.tol_g = 1e-9 / h->slack_scale;
     LM_CUDA(h, launch_crossover(ca, h->xw, nullptr, nullptr, st), "crossover kernels");
     mark(h, 4);
     // 5. retry list: the interior point from the start with the accurate
     //    residual phase, then the crossover again
     ia.list = h->retry; ia.list_len = h->dcnt + 5;
-    ia.mu_ref = h->opt.refine_mu; ia.counter = h->dcnt + 1;
+    ia.mu_ref = h->opt.refine_mu / (h->slack_scale * h->slack_scale); ia.counter = h->dcnt + 1;
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "retry interior-point kernel (float32)");
     ia.counter = h->dcnt + 4;
     LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "retry interior-point kernel (double-float)");
-    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = h->dcnt + 3;
+    // a pixel the retry crossover cannot verify keeps its interior-point
+    // iterate and is reported as not converged (negative iteration count)
+    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = h->dcnt + 2;
+    ca.it_mark = h->it;
     LM_CUDA(h, launch_crossover(ca, h->xw, h->retry, h->dcnt + 5, st), "retry crossover kernels");
     mark(h, 5);
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
@@ -504,6 +546,15 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
                   2 + crossover_launches(false) + (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
                       "copy iterations");
+    if (h->slack) {
+        LM_CUDA(h, launch_strip_slack(h->xa, h->sxa, N, h->user_P, h->slack_scale,
+                                      h->opt.constraint == LINMIN_POS,
+                                      abundances ? u_x : nullptr, u_sx, d_it, h->dcnt + 2, st),
+                "slack outputs");
+        ++h->launches;
+    }
+    d_x = u_x;
+    d_sx = u_sx;
 
     if (!host_any) return LINMIN_OK;
     if (abundances && !dev_out[0])
@@ -689,7 +740,7 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
 {
     *out = nullptr;
     linmin_ctx *h = new linmin_ctx();
-    h->L = L; h->P = P; h->opt = o;
+    h->L = L; h->P = P; h->user_P = P; h->opt = o;
     h->stream = (cudaStream_t)o.cuda_stream;
     cudaGetDevice(&h->device);
     if (!ipm_bucket(P, &h->bucket)) { delete h; return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P"); }
@@ -751,7 +802,7 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
                     h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
                     h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT, h->bsl,
-                    h->fexp};
+                    h->fexp, h->xa, h->sxa};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
     if (h->pool) pool_release(h->device);

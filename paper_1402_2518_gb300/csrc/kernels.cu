@@ -79,7 +79,10 @@ __global__ void prep_finish_kernel(int P, int PP, const double *__restrict__ G64
         if (i < P) {
             for (int j = 0; j < P; ++j) r += G64[(size_t)i * P + j] / s + RHO;
             r /= P;
-            gdiag[i] = (float)(G64[(size_t)i * P + i] / s);
+            // curvature of the support test; a zero spectrum (the slack of
+            // the sum <= 1 constraint) has none: unit curvature there
+            const double gi = G64[(size_t)i * P + i] / s;
+            gdiag[i] = gi > 0.0 ? (float)gi : 1.f;
         }
         grs[i] = (float)r;
     }
@@ -194,6 +197,41 @@ cudaError_t launch_prep_t_diag(const float *S, const float *sigma, int L, int P,
     const long long lp = (long long)L * P;
     const int tb = (int)((lp + 255) / 256 < 1024 ? (lp + 255) / 256 : 1024);
     prep_t_diag_kernel<<<tb, 256, 0, st>>>(S, sigma, L, P, T);
+    return cudaGetLastError();
+}
+
+// Outputs of the slo / pos constraint sets: the internal problem has the
+// slack as coordinate P (last); user x = M x', sx = M sx' for the first P
+// coordinates; with bound_check (pos), a pixel whose slack is zero reached
+// the bound M: negative iteration count, counted as not converged.
+__global__ void strip_slack_kernel(const float *__restrict__ xa, const float *__restrict__ sxa,
+                                   long long N, int P, float M, bool bound_check,
+                                   float *__restrict__ x, float *__restrict__ sx,
+                                   int *__restrict__ it, unsigned long long *__restrict__ nbad)
+{
+    const long long total = N * (long long)P;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long n = e / P;
+        const int j = (int)(e % P);
+        const size_t src = (size_t)n * (P + 1) + j;
+        if (x) x[e] = M * xa[src];
+        if (sx) sx[e] = M * sxa[src];
+        if (bound_check && j == 0 && !(xa[(size_t)n * (P + 1) + P] > 0.f)) {
+            if (it) it[n] = -abs(it[n]) - 1;
+            atomicAdd(nbad, 1ULL);
+        }
+    }
+}
+
+cudaError_t launch_strip_slack(const float *xa, const float *sxa, long long N, int P, float M,
+                               bool bound_check, float *x, float *sx, int *it,
+                               unsigned long long *nbad, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    const long long total = N * (long long)P;
+    const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    strip_slack_kernel<<<blocks, 256, 0, st>>>(xa, sxa, N, P, M, bound_check, x, sx, it, nbad);
     return cudaGetLastError();
 }
 
@@ -584,7 +622,11 @@ crossover_pass_kernel(const CrossArgs a)
         const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
         a.retry_list[pos] = n;
     } else if (a.n_unverified) {
-        atomicAdd(a.n_unverified, 1ULL);
+        // the iterate stays as the result: reported as not converged
+        if (!a.it_mark || a.it_mark[n] > 0) {
+            atomicAdd(a.n_unverified, 1ULL);
+            if (a.it_mark) a.it_mark[n] = -a.it_mark[n];
+        }
     }
     if (a.x_out != a.x_in)
         for (int i = 0; i < P; ++i) a.x_out[base + i] = a.x_in[base + i];
@@ -926,7 +968,11 @@ crossover_group_kernel(const CrossArgs a)
                     const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
                     a.retry_list[pos] = n;
                 } else if (a.n_unverified) {
-                    atomicAdd(a.n_unverified, 1ULL);
+                    // the iterate stays as the result: reported as not converged
+                    if (!a.it_mark || a.it_mark[n] > 0) {
+                        atomicAdd(a.n_unverified, 1ULL);
+                        if (a.it_mark) a.it_mark[n] = -a.it_mark[n];
+                    }
                 }
             }
             for (int i = t; i < P; i += XG) {

@@ -69,6 +69,10 @@ bool tc2_usable(const float *cube, long long N, int L);
 cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
                                const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st);
+// slo / pos outputs from the slack-augmented internal problem
+cudaError_t launch_strip_slack(const float *xa, const float *sxa, long long N, int P, float M,
+                               bool bound_check, float *x, float *sx, int *it,
+                               unsigned long long *nbad, cudaStream_t st);
 cudaError_t launch_project(const float *cube, long long N, int L, int P,
                            const float *Bhi, const float *Blo, float *c_hi,
                            float *c_lo, cudaStream_t st);
@@ -97,6 +101,8 @@ struct CrossArgs {
     long long *retry_list;         // pixels the crossover could not finish (or NULL)
     unsigned long long *retry_len;
     unsigned long long *n_unverified;   // counted when retry_list is NULL
+    int *it_mark;                  // with n_unverified: iteration counts, negated
+                                   // (not converged) for a pixel left unverified
     double tol_x, tol_g;
 };
 

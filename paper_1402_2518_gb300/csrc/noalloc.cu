@@ -185,7 +185,8 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     NA_CUDA(launch_ipm(b, false, ia, st));
     ia.counter = cnt + 4;
     NA_CUDA(launch_ipm(b, true, ia, st));
-    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = cnt + 3;
+    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = cnt + 2;
+    ca.it_mark = its;
     NA_CUDA(launch_crossover(ca, xw, retry, cnt + 5, st));
     if (residual_rms) NA_CUDA(launch_rms(cube, library, x_out, N, L, P, residual_rms, st));
     if (iterations)

@@ -23,6 +23,9 @@ LINMIN_ERR_NOT_CONVERGED = 6
 LINMIN_ERR_UNSUPPORTED = 7
 LINMIN_PROJ_DF = 0
 LINMIN_STO = 0
+LINMIN_SLO = 1
+LINMIN_POS = 2
+LINMIN_POS_SCALE = 64
 LINMIN_MAX_P = 64
 LINMIN_MAX_L = 4096
 
@@ -294,7 +297,7 @@ class Unmixer:
 
     def __init__(self, library, max_iter: int = 100, tol: float = 1e-9,
                  refine_mu: float = 1e-9, stream=None, profile: bool = False,
-                 precision: int | None = None):
+                 precision: int | None = None, constraint: int = 0):
         import torch
         S = library if hasattr(library, "data_ptr") else torch.as_tensor(library)
         S = S.to(torch.float32).contiguous()
@@ -304,6 +307,7 @@ class Unmixer:
         opt.profile = int(bool(profile))
         if precision is not None:
             opt.precision = int(precision)
+        opt.constraint = int(constraint)
         if stream is not None:
             opt.cuda_stream = ctypes.c_void_p(int(stream.cuda_stream))
         self.h = linmin_create(S, self.L, self.P, opt)

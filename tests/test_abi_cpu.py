@@ -39,12 +39,17 @@ def test_no_other_exports():
 
 def test_header_constants_match_binding():
     txt = open(HEADER).read()
+    for name in ("LINMIN_STO", "LINMIN_SLO", "LINMIN_POS", "LINMIN_PROJ_DF", "LINMIN_PROJ_TC",
+                 "LINMIN_PROJ_BF16"):
+        m = re.search(rf"\b{name}\s*=\s*(\d+)", txt)
+        assert m and int(m.group(1)) == getattr(linmin, name), name
     for name in ("LINMIN_OK", "LINMIN_ERR_INVALID", "LINMIN_ERR_OOM", "LINMIN_ERR_CUDA",
                  "LINMIN_ERR_RANK", "LINMIN_ERR_TIMEOUT", "LINMIN_ERR_NOT_CONVERGED",
                  "LINMIN_ERR_UNSUPPORTED"):
         m = re.search(rf"{name}\s*=\s*(\d+)", txt)
         assert m and int(m.group(1)) == getattr(linmin, name)
-    for name in ("LINMIN_MAX_P", "LINMIN_MAX_L", "LINMIN_NOALLOC_SCRATCH_MB", "LINMIN_PHASE_RING"):
+    for name in ("LINMIN_MAX_P", "LINMIN_MAX_L", "LINMIN_NOALLOC_SCRATCH_MB", "LINMIN_PHASE_RING",
+                 "LINMIN_POS_SCALE"):
         m = re.search(rf"#define {name} (\d+)", txt)
         assert m and int(m.group(1)) == getattr(linmin, name)
 
@@ -153,3 +158,23 @@ def test_lanes_entry_points_reject_null_handle():
     assert lib.linmin_set_lanes(None, 4) == linmin.LINMIN_ERR_INVALID
     assert lib.linmin_autotune(None, None, 0, None, None, None, 0, None) == \
         linmin.LINMIN_ERR_INVALID
+
+
+def test_constraint_rank_refusal_on_host():
+    """slo / pos need rank S = P: the level/slope extras (0.5 flat - 0.5 u
+    - 0.5 (1 - u) = 0, exact up to float32 rounding) are refused on the
+    host, before any device work; sto accepts them."""
+    import numpy as np
+    import synth
+    lib = pkg.load()
+    cube = synth.make_cube(synth.OMEGA_262K, n_pix=1)
+    h = ctypes.c_void_p()
+    for c in (linmin.LINMIN_SLO, linmin.LINMIN_POS):
+        opt = pkg.linmin_default_options()
+        opt.constraint = c
+        assert lib.linmin_create(cube.S.ctypes.data_as(ctypes.c_void_p), cube.L, cube.P,
+                                 ctypes.byref(opt), ctypes.byref(h)) == linmin.LINMIN_ERR_RANK
+    opt = pkg.linmin_default_options()
+    opt.constraint = 7
+    assert lib.linmin_create(cube.S.ctypes.data_as(ctypes.c_void_p), cube.L, cube.P,
+                             ctypes.byref(opt), ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
