@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer e2e leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-cov", action="store_true", help="skip the full-covariance leg")
+    ap.add_argument("--no-constraints", action="store_true", help="skip the slo / pos leg")
     ap.add_argument("--precision", default="tc", choices=["df", "tc", "bf16"],
                     help="projection: double-float CUDA cores, exact tensor-core slices, bf16")
     ap.add_argument("--serving-cubes", type=int, default=64)
@@ -336,6 +337,41 @@ def run_cov(pkg, dev, n_pix: int, rho: float, steps: int):
             "status": st, "not_converged": nbad}
 
 
+def run_constraints(pkg, dev, n_pix: int, steps: int):
+    """The slo (sum x <= 1) and pos (x >= 0) constraint sets on the same
+    cube with the library's decreasing slope dropped (they need rank S = P,
+    which the flat + two slopes break): pixels/s of each."""
+    import torch
+    cube = synth.make_cube(SPEC, n_pix=n_pix or None)
+    keep = [j for j in range(cube.P) if j != cube.P - 2]
+    S = torch.from_numpy(np.ascontiguousarray(cube.S[keep])).to(dev)
+    X = torch.from_numpy(cube.X).to(dev)
+    sg = torch.from_numpy(cube.sigma).to(dev)
+    N, P = cube.N, len(keep)
+    out = {"library": f"{P} spectra (decreasing slope dropped: rank S = P)", "pixels": N}
+    for name, c in (("slo", 1), ("pos", 2)):
+        stream = torch.cuda.Stream(device=dev)
+        um = pkg.Unmixer(S, stream=stream, constraint=c)
+        x = torch.empty((N, P), device=dev); sx = torch.empty((N, P), device=dev)
+        rms = torch.empty((N,), device=dev); it = torch.empty((N,), dtype=torch.int32, device=dev)
+        for _ in range(2):
+            pkg.linmin_unmix(um.h, X, N, sg, x, sx, rms, it)
+        st, nbad = um.wait()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            pkg.linmin_unmix(um.h, X, N, sg, x, sx, rms, it)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"value": N / (ms / 1e3), "unit": "pixels/s", "ms_per_step": ms,
+                     "status": st, "not_converged": nbad,
+                     "mean_iters": float(it.to(torch.float64).abs().mean().item())}
+        um.close()
+    return out
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -420,6 +456,9 @@ def main():
     full_cov = None
     if not args.no_cov and rank == 0:
         full_cov = run_cov(pkg, dev, args.pixels, 0.5, max(3, args.steps // 4))
+    constraints = None
+    if not args.no_constraints and rank == 0:
+        constraints = run_constraints(pkg, dev, args.pixels, max(3, args.steps // 4))
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,
@@ -468,6 +507,7 @@ def main():
         "cpu_baseline": cpu,
         "serving": serving,
         "full_covariance": full_cov,
+        "constraints": constraints,
     }
     print(json.dumps(line))
     if ws > 1:
