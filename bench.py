@@ -37,12 +37,12 @@ METRIC = "pixels/s IPLS unmix at <=1e-4 abs err vs FP64 oracle; served p50/p99 l
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes per pixel of the main interior-point launch, from the ncu
-# capture summarised in profiles/ipm_kernel_omega65k_full.md
+# capture summarised in profiles/ipm_and_projection_omega65k_full.md
 # (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels; traffic
 # grows with the pixel count).  Valid only for the kernel source it was
 # measured on (hash of csrc/ipm.cuh).
-IPM_TRAFFIC = {"ipm_sha256_12": "aaae08760011",
-               "bytes_per_pixel": (9.681152e6 + 0.081664e6) / 65536}
+IPM_TRAFFIC = {"ipm_sha256_12": "633fdf1419b5",
+               "bytes_per_pixel": (9.679104e6 + 0.087296e6) / 65536}
 
 
 def ipm_traffic(n_pix: int):
