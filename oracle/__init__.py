@@ -185,7 +185,7 @@ def unmix(S, sigma, X, nthreads: int = 0, max_iter: int = MAX_ITER,
     return out
 
 
-POS_SCALE = 4096.0
+POS_SCALE = 64.0
 
 
 def unmix_constraint(S, sigma, X, constraint: str = "sto", max_iter: int = MAX_ITER):
