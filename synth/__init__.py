@@ -266,3 +266,79 @@ def make_cube_cov(spec: CubeSpec, rho: float, n_pix: int | None = None):
     Cinv = np.linalg.inv(C)
     Cinv = 0.5 * (Cinv + Cinv.T)
     return Cube(spec, base.S, base.sigma, X, A), C, Cinv
+
+
+# ------------------------------------------- surface mixtures (Sec. 3.1)
+def surface_mixtures(n: int = 1000, L: int = 184, n_ref: int = 32, flat: float = 0.35,
+                     frac_max: float = 0.1, noise_mean: float = 1.3e-3,
+                     seed: int = BASE_SEED + 5):
+    """The synthetic surface of Sec. 3.1: every spectrum is a binary mixture
+    of a flat component at reflectance ``flat`` and one of ``n_ref``
+    reference spectra (drawn uniformly), with the reference's share a drawn
+    uniformly in (0, frac_max): y = (1 - a) flat + a S_i + noise, so that
+    each reference is present in about n / n_ref spectra.  The noise is
+    N(0, sigma_l^2) with sigma_l uniform in [0.5, 1.5] * noise_mean (a
+    wavelength-average standard deviation of noise_mean).
+
+    The library is the n_ref references followed by the four level/slope
+    extras of this module (aerosol, u, 0.5 (1 - u), 1); the flat component
+    is the sum-to-one combination 0.025 * 1 + 0.325 u + 0.65 * 0.5 (1 - u)
+    (level 0.35, sum 1) scaled by (1 - a), so ``A_true`` is on the simplex.
+
+    Returns (cube, truth): truth[n] has bit i set when reference i is
+    present in spectrum n (uint64)."""
+    if abs(flat - 0.35) > 1e-12:
+        raise ValueError("the extras' combination above is worked out for flat = 0.35")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    S = library(rng, L, n_ref, 4)
+    if not check_unique(S):
+        raise RuntimeError("surface library: rank [S^T; 1^T] < P")
+    sigma = noise_mean * rng.uniform(0.5, 1.5, size=L)
+    ref = rng.integers(0, n_ref, size=n)
+    a = frac_max * (1.0 - rng.random(n))              # (0, frac_max]
+    A = np.zeros((n, n_ref + 4))
+    A[np.arange(n), ref] = a
+    A[:, n_ref + 1] = 0.325 * (1.0 - a)               # slope increasing u
+    A[:, n_ref + 2] = 0.65 * (1.0 - a)                # 0.5 (1 - u)
+    A[:, n_ref + 3] = 0.025 * (1.0 - a)               # flat 1
+    E = rng.standard_normal((n, L)) * sigma[None, :]
+    X = (A @ S + E).astype(np.float32)
+    spec = CubeSpec(f"surface_{n}_L{L}_P{n_ref + 4}", n, L, n_ref, 4,
+                    sigma_lo=0.5 * noise_mean, sigma_hi=1.5 * noise_mean, seed=seed)
+    truth = np.left_shift(np.uint64(1), ref.astype(np.uint64))
+    return Cube(spec, S.astype(np.float32), sigma.astype(np.float32), X, A), truth
+
+
+def truth_masks(A_true: np.ndarray, n_minerals: int) -> np.ndarray:
+    """Bit i of entry n set when mineral i < n_minerals has a non-zero true
+    abundance in pixel n (uint64)."""
+    m = np.zeros(A_true.shape[0], dtype=np.uint64)
+    for i in range(n_minerals):
+        m |= (A_true[:, i] > 0).astype(np.uint64) << np.uint64(i)
+    return m
+
+
+def detection_inputs(seed: int, N: int, P: int, n_minerals: int, x_min: np.ndarray,
+                     rms_max: float):
+    """Seeded arrays shaped like unmixing outputs for the detection tests:
+    abundances on the simplex, many exactly at or one ulp around a
+    threshold, uncertainties equal to or near their abundance, RMS values
+    at and around rms_max, a few negative iteration counts, random truth
+    masks.  Returns (x, sx, rms, iterations, truth)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.dirichlet(np.full(P, 0.3), size=N).astype(np.float32) if N else np.zeros((0, P), np.float32)
+    xm = np.asarray(x_min, dtype=np.float32)
+    for i in range(min(n_minerals, P)):           # exact ties and one-ulp neighbours
+        sel = rng.random(N) < 0.1
+        k = int(sel.sum())
+        x[sel, i] = rng.choice(np.array([xm[i], np.nextafter(xm[i], np.float32(1)),
+                                         np.nextafter(xm[i], np.float32(0))], np.float32), k)
+    sx = (x * rng.uniform(0.3, 1.3, size=x.shape)).astype(np.float32)
+    eq = rng.random(x.shape) < 0.05
+    sx[eq] = x[eq]
+    rms = np.float32(rms_max) * rng.uniform(0.5, 1.5, size=N).astype(np.float32)
+    rms[rng.random(N) < 0.05] = np.float32(rms_max)
+    it = rng.integers(5, 30, size=N).astype(np.int32)
+    it[rng.random(N) < 0.02] *= -1
+    truth = rng.integers(0, 2 ** 63, size=N, dtype=np.int64).astype(np.uint64)
+    return x, sx, rms.astype(np.float32), it, truth
