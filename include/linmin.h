@@ -385,6 +385,95 @@ LINMIN_API linmin_status linmin_unmix_noalloc(const float *library, int L, int P
                                               float *uncertainties, float *residual_rms,
                                               int *iterations, void *cuda_stream);
 
+/* ------------------------------------------------------------------ */
+/*
+ * Detection products.  After unmixing, a mineral counts as detected in a
+ * pixel under the conditions the paper lists for real images (Sec. 5,
+ * introduction): its abundance is above a threshold chosen per mineral,
+ * its uncertainty is below its abundance, and the pixel's RMS is below
+ * the noise level.  The thresholds come from the synthetic surface
+ * mixtures of Sec. 3.1 (eq. Threshold), where the truth is known.  The
+ * paper has no C interface for these; the entry points below are
+ * stream-ordered device computations (no synchronisation).
+ */
+
+/* The paper's additional spectra (Sec. 2.5; Appendix, names 33-44), one row
+ * of L values each in out (host, n_extras x L), with u = (w_l - w_0) /
+ * (w_{L-1} - w_0) over the wavelengths w (host, L values increasing; NULL:
+ * evenly spaced, u_l = l / (L - 1)):
+ *   n_extras = 4:  Flat 1, Flat 0.0001, slope increasing u, slope
+ *                  decreasing 1 - u;
+ *   n_extras = 12: those four, then cos, sin, -cos, -sin of pi u / 2 (the
+ *                  "1/4" functions: a quarter period over the domain), then
+ *                  of pi u (the "1/2" functions).
+ * Computed in double, rounded to float.  Under x >= 0, sum x = 1 neither
+ * set leaves the minimiser unique: rank [S^T; 1^T] is 3 for the four and 7
+ * for the twelve, so linmin_create refuses a library that holds all of
+ * them (LINMIN_ERR_RANK).  L >= 2, else LINMIN_ERR_INVALID. */
+LINMIN_API linmin_status linmin_extra_spectra(int L, const float *wavelengths, int n_extras,
+                                              float *out);
+
+/* Per-mineral detection summary (device memory, written by linmin_detect).
+ * Entries at index >= n_minerals are zero. */
+typedef struct {
+    long long count[LINMIN_MAX_P];      /* pixels where mineral i is detected */
+    long long argmax[LINMIN_MAX_P];     /* smallest pixel index holding the
+                                           largest detected x_i; -1 if none */
+    long long n_true[LINMIN_MAX_P];     /* with truth: pixels where i is present */
+    long long true_pos[LINMIN_MAX_P];   /* with truth: present and detected */
+    long long false_pos[LINMIN_MAX_P];  /* with truth: absent and detected */
+    double xsum[LINMIN_MAX_P];          /* sum of the detected x_i (atomic
+                                           order: last-bit differences run to
+                                           run) */
+    float xmax[LINMIN_MAX_P];           /* largest detected x_i; 0 if none */
+    unsigned long long key[LINMIN_MAX_P]; /* scratch of the arg-max */
+} linmin_detection;
+
+/* Detect minerals pixel by pixel.  All array pointers are device memory:
+ *   x, sx      N x P abundances and uncertainties (linmin_unmix outputs);
+ *              sx may be NULL (no uncertainty condition);
+ *   rms        N residual RMS, may be NULL (no RMS condition);
+ *   iterations N, may be NULL; a pixel with iterations < 0 detects nothing;
+ *   truth      N bit masks, may be NULL: bit i set when mineral i is
+ *              present in the pixel (synthetic cubes), for the rates;
+ *   x_min      host, n_minerals thresholds C_i (finite, >= 0);
+ *   mask       N bit masks out, may be NULL: bit i set when mineral i is
+ *              detected;
+ *   out        one linmin_detection, may be NULL.
+ * Mineral i < n_minerals is detected in pixel n when
+ *   x[n,i] > x_min[i]  and  sx[n,i] < x[n,i]  and  rms[n] < rms_max
+ * (strict comparisons of the float32 values; absent arrays drop their
+ * condition).  Columns >= n_minerals (the additional spectra) are never
+ * detected.  1 <= P <= LINMIN_MAX_P, 0 <= n_minerals <= P,
+ * 0 <= N < 2^32; stream: cudaStream_t or NULL. */
+LINMIN_API linmin_status linmin_detect(const float *x, const float *sx, const float *rms,
+                                       const int *iterations, const unsigned long long *truth,
+                                       long long N, int P, int n_minerals, const float *x_min,
+                                       float rms_max, unsigned long long *mask,
+                                       linmin_detection *out, void *stream);
+
+/* Sums over the pixels where mineral i is present (pos) and absent (neg)
+ * in a synthetic cube, for eq. Threshold (device memory). */
+typedef struct {
+    long long n_pos[LINMIN_MAX_P], n_neg[LINMIN_MAX_P];
+    double sum_pos[LINMIN_MAX_P], sumsq_pos[LINMIN_MAX_P];
+    double sum_neg[LINMIN_MAX_P], sumsq_neg[LINMIN_MAX_P];
+} linmin_threshold_sums;
+
+/* Accumulate linmin_threshold_sums of x (device, N x P) split by truth
+ * (device, N bit masks), for minerals i < n_minerals; out is device
+ * memory, overwritten.  Same limits as linmin_detect. */
+LINMIN_API linmin_status linmin_threshold_stats(const float *x, const unsigned long long *truth,
+                                                long long N, int P, int n_minerals,
+                                                linmin_threshold_sums *out, void *stream);
+
+/* eq. Threshold, per mineral i < n_minerals, from stats on the host:
+ *   C_i = 1/2 (mean_pos - 2 std_pos + mean_neg + 6 std_neg)
+ * with population standard deviations (divided by the count).  A mineral
+ * with no present or no absent pixel gets C_i = NaN. */
+LINMIN_API linmin_status linmin_thresholds(const linmin_threshold_sums *stats, int n_minerals,
+                                           float *c_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,4 +12,7 @@ from .linmin import (EXPORTED, LinminError, Server, Unmixer, library_path, linmi
                      linmin_server_create, linmin_server_default_options,
                      linmin_server_destroy, linmin_server_get_stats, linmin_server_handle_bytes, linmin_server_last_error,
                      linmin_server_poll, linmin_server_submit, linmin_server_wait,
-                     linmin_wait, load)
+                     linmin_wait, load,
+                     linmin_detect, linmin_extra_spectra, linmin_threshold_stats,
+                     linmin_thresholds, linmin_detection, linmin_threshold_sums,
+                     detection_summary, threshold_sums)

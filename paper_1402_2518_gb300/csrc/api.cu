@@ -725,6 +725,8 @@ const char *linmin_last_error(linmin_handle h)
 
 }  // extern "C"
 
+void lm::set_global_error(const std::string &m) { g_create_error = m; }
+
 // outside the C block: a C++ function of namespace lm
 linmin_status lm::reserve(linmin_handle h, long long N, bool host_io)
 {

@@ -30,4 +30,8 @@ size_t handle_bytes(int L, int P, long long N, bool host_io);
 // that later calls with at most N pixels allocate nothing.
 linmin_status reserve(linmin_handle h, long long N, bool host_io);
 
+// Record the message linmin_last_error(NULL) returns (entry points
+// without a handle).
+void set_global_error(const std::string &m);
+
 }  // namespace lm

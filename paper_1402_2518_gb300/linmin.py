@@ -38,7 +38,9 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_server_default_options", "linmin_server_create", "linmin_server_submit",
             "linmin_server_poll", "linmin_server_wait", "linmin_server_get_stats",
             "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
-            "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov")
+            "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
+            "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
+            "linmin_thresholds")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -72,6 +74,21 @@ class linmin_server_stats(ctypes.Structure):
                                             ("max_running", ctypes.c_int)]
 
 
+_I64x = ctypes.c_longlong * LINMIN_MAX_P
+_F64x = ctypes.c_double * LINMIN_MAX_P
+
+
+class linmin_detection(ctypes.Structure):
+    _fields_ = [("count", _I64x), ("argmax", _I64x), ("n_true", _I64x), ("true_pos", _I64x),
+                ("false_pos", _I64x), ("xsum", _F64x), ("xmax", ctypes.c_float * LINMIN_MAX_P),
+                ("key", ctypes.c_ulonglong * LINMIN_MAX_P)]
+
+
+class linmin_threshold_sums(ctypes.Structure):
+    _fields_ = [("n_pos", _I64x), ("n_neg", _I64x), ("sum_pos", _F64x), ("sumsq_pos", _F64x),
+                ("sum_neg", _F64x), ("sumsq_neg", _F64x)]
+
+
 class LinminError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -84,11 +101,11 @@ def library_path() -> str:
 
 def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     """Load liblinmin.so (building it in-tree first if it is missing)."""
+    if path is None and build_if_missing:
+        path = _build.build()             # no-op when the stamp matches the sources
     path = path or _build.LIB
     if not os.path.exists(path):
-        if not build_if_missing:
-            raise OSError(f"{path} not built")
-        path = _build.build()
+        raise OSError(f"{path} not built")
     lib = ctypes.CDLL(path)
     H = ctypes.c_void_p
     P = ctypes.c_void_p
@@ -149,6 +166,16 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_last_launches.restype = ctypes.c_int
     lib.linmin_version.argtypes = []
     lib.linmin_version.restype = ctypes.c_char_p
+    lib.linmin_extra_spectra.argtypes = [ctypes.c_int, P, ctypes.c_int, P]
+    lib.linmin_extra_spectra.restype = ctypes.c_int
+    lib.linmin_detect.argtypes = [P, P, P, P, P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                  P, ctypes.c_float, P, P, ctypes.c_void_p]
+    lib.linmin_detect.restype = ctypes.c_int
+    lib.linmin_threshold_stats.argtypes = [P, P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                           P, ctypes.c_void_p]
+    lib.linmin_threshold_stats.restype = ctypes.c_int
+    lib.linmin_thresholds.argtypes = [ctypes.POINTER(linmin_threshold_sums), ctypes.c_int, P]
+    lib.linmin_thresholds.restype = ctypes.c_int
     return lib
 
 
@@ -289,6 +316,78 @@ def linmin_last_launches(h) -> int:
 
 def linmin_version() -> str:
     return lib().linmin_version().decode()
+
+
+def _ptr_any(a, names):
+    """_ptr accepting any of the dtype names (bit masks: int64 or uint64)."""
+    if a is None:
+        return None
+    got = str(a.dtype).split(".")[-1] if hasattr(a, "data_ptr") else a.dtype.name
+    if got not in names:
+        raise TypeError(f"expected one of {names}, got {got}")
+    return _ptr(a, got)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def linmin_extra_spectra(L: int, n_extras: int = 12, wavelengths=None):
+    """The paper's additional spectra, (n_extras, L) float32 numpy."""
+    import numpy as np
+    out = np.empty((n_extras, L), dtype=np.float32)
+    w = None if wavelengths is None else np.ascontiguousarray(wavelengths, dtype=np.float32)
+    _check(lib().linmin_extra_spectra(int(L), _ptr(w), int(n_extras), _ptr(out)))
+    return out
+
+
+def linmin_detect(x, sx, rms, iterations, truth, N: int, P: int, n_minerals: int, x_min,
+                  rms_max: float, mask=None, out=None, stream=None) -> int:
+    """Queue the detection kernel (device arrays; out: a device byte buffer
+    of sizeof(linmin_detection), see detection_summary)."""
+    import numpy as np
+    xm = np.ascontiguousarray(np.asarray(x_min, dtype=np.float32).reshape(-1))
+    return _check(lib().linmin_detect(_ptr(x), _ptr(sx), _ptr(rms), _ptr(iterations, "int32"),
+                                      _ptr_any(truth, ("int64", "uint64")), int(N), int(P),
+                                      int(n_minerals), _ptr(xm), float(rms_max),
+                                      _ptr_any(mask, ("int64", "uint64")),
+                                      _ptr(out, "uint8"), _stream_ptr(stream)))
+
+
+def linmin_threshold_stats(x, truth, N: int, P: int, n_minerals: int, out, stream=None) -> int:
+    """Queue the threshold sums (out: a device byte buffer of
+    sizeof(linmin_threshold_sums))."""
+    return _check(lib().linmin_threshold_stats(_ptr(x), _ptr_any(truth, ("int64", "uint64")),
+                                               int(N), int(P), int(n_minerals),
+                                               _ptr(out, "uint8"), _stream_ptr(stream)))
+
+
+def linmin_thresholds(sums: linmin_threshold_sums, n_minerals: int):
+    """eq. Threshold from sums on the host; float32 numpy of n_minerals."""
+    import numpy as np
+    c = np.empty(max(1, n_minerals), dtype=np.float32)
+    _check(lib().linmin_thresholds(ctypes.byref(sums), int(n_minerals), _ptr(c)))
+    return c[:n_minerals]
+
+
+def _struct_from(buf, cls):
+    data = buf.cpu().numpy().tobytes() if hasattr(buf, "cpu") else bytes(buf)
+    return cls.from_buffer_copy(data)
+
+
+def detection_summary(buf) -> dict:
+    """Decode a linmin_detection byte buffer (device or host) into numpy arrays."""
+    import numpy as np
+    d = _struct_from(buf, linmin_detection)
+    out = {f: np.array(getattr(d, f)) for f, _ in linmin_detection._fields_ if f != "key"}
+    return out
+
+
+def threshold_sums(buf) -> linmin_threshold_sums:
+    """Decode a linmin_threshold_sums byte buffer (device or host)."""
+    return _struct_from(buf, linmin_threshold_sums)
 
 
 class Unmixer:

@@ -107,7 +107,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     structs = {"linmin_options": linmin.linmin_options,
                "linmin_server_options": linmin.linmin_server_options,
                "linmin_request": linmin.linmin_request,
-               "linmin_server_stats": linmin.linmin_server_stats}
+               "linmin_server_stats": linmin.linmin_server_stats,
+               "linmin_detection": linmin.linmin_detection,
+               "linmin_threshold_sums": linmin.linmin_threshold_sums}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "linmin.h"', 'int main(void) {']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
