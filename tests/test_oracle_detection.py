@@ -2,7 +2,9 @@
 hand-worked cases: the additional spectra of the Appendix table at u = 0,
 1/2, 1; the rank deficiency those spectra bring under sum-to-one; the three
 detection conditions of Sec. 5 on a five-pixel case; eq. Threshold of
-Sec. 3.1 on a four-pixel case; and the surface-mixture recipe of Sec. 3.1."""
+Sec. 3.1 on a four-pixel case; the surface-mixture recipe of Sec. 3.1; and
+the library auto-fit of Sec. 2.5 (oracle.autofit) against exact
+dependencies, brute-force NNLS and the least-squares normal equations."""
 import math
 
 import numpy as np
@@ -110,3 +112,75 @@ def test_surface_mixtures_recipe():
     counts = np.bincount(np.log2(truth.astype(np.float64)).astype(int), minlength=32)
     assert counts.sum() == 1000 and counts.min() >= 10      # about 1000 / 32 each
     assert abs(cube.sigma.mean() - 1.3e-3) < 1e-4
+
+
+# ------------------------------------------------------------- auto-fit
+def _brute_nnls(A, y):
+    """min |y - A a|, a >= 0 by enumerating supports (tiny column counts)."""
+    import itertools
+    m = A.shape[1]
+    best, best_a = np.inf, None
+    for k in range(0, m + 1):
+        for sup in itertools.combinations(range(m), k):
+            a = np.zeros(m)
+            if sup:
+                sol = np.linalg.lstsq(A[:, sup], y, rcond=None)[0]
+                if (sol < -1e-12).any():
+                    continue
+                a[list(sup)] = np.maximum(sol, 0)
+            r = np.linalg.norm(y - A @ a)
+            if r < best - 1e-12:
+                best, best_a = r, a
+    return best_a, best
+
+
+def test_autofit_hand_case():
+    """S2 = S0 + S1 exactly: S2 is fitted exactly with coefficients (1, 1)
+    in both problems; S0 = S2 - S1 needs a negative coefficient, so only
+    the unconstrained residue vanishes."""
+    import oracle.autofit as oa
+    S0 = np.array([1, 0, 2, 1, 0, 3], np.float32)
+    S1 = np.array([0, 2, 1, 1, 3, 0], np.float32)
+    S = np.stack([S0, S1, S0 + S1])
+    r = oa.autofit(S)
+    assert np.abs(r["resid_ls"]).max() < 1e-12
+    assert np.abs(r["resid_nn"][2]).max() < 1e-12
+    np.testing.assert_allclose(r["coef_nn"][2], [1, 1, 0], atol=1e-12)
+    # S0 on {S1, S2} with a >= 0: the support {S2} alone, a = <S0,S2>/<S2,S2>
+    S2 = (S0 + S1).astype(np.float64)
+    a2 = float(S0 @ S2 / (S2 @ S2))
+    assert a2 > 0
+    np.testing.assert_allclose(r["coef_nn"][0], [0, 0, a2], atol=1e-12)
+    np.testing.assert_allclose(r["resid_nn"][0], S0 - a2 * S2, atol=1e-12)
+
+
+def test_autofit_brute_force_and_invariants():
+    import oracle.autofit as oa
+    rng = np.random.Generator(np.random.PCG64(12))
+    for P in (2, 3, 5, 6):
+        S = rng.uniform(0.0, 1.0, (P, 9)).astype(np.float32)
+        r = oa.autofit(S)
+        S64 = S.astype(np.float64)
+        for n in range(P):
+            others = [j for j in range(P) if j != n]
+            A = S64[others].T
+            a, best = _brute_nnls(A, S64[n])
+            assert abs(np.linalg.norm(r["resid_nn"][n]) - best) < 1e-10
+            np.testing.assert_allclose(r["coef_nn"][n, others], a, atol=1e-9)
+            # least squares: the residue is orthogonal to every other spectrum
+            assert np.abs(A.T @ r["resid_ls"][n]).max() < 1e-10
+            # the unconstrained problem is a relaxation of the constrained one
+            assert np.linalg.norm(r["resid_ls"][n]) <= np.linalg.norm(r["resid_nn"][n]) + 1e-12
+            np.testing.assert_allclose(r["rms_nn"][n], best / 3.0, rtol=1e-10)   # sqrt(9) bands
+
+
+def test_autofit_dependent_extras():
+    """The level/slope spectra u, 0.5 (1 - u) and 1 are linearly dependent:
+    each is fitted exactly by the others without constraints; under x >= 0
+    the slopes are not (u = 1 - 2 * 0.5 (1 - u) needs a negative weight)."""
+    import oracle.autofit as oa
+    E = synth.extra_spectra(184)[1:]         # u, 0.5 (1 - u), 1
+    r = oa.autofit(E.astype(np.float32))
+    assert r["rms_ls"].max() < 1e-7
+    assert r["rms_nn"][0] > 1e-2 and r["rms_nn"][1] > 1e-2
+    assert r["rms_nn"][2] < 1e-7             # 1 = u + 2 * 0.5 (1 - u), weights >= 0
