@@ -474,6 +474,28 @@ LINMIN_API linmin_status linmin_threshold_stats(const float *x, const unsigned l
 LINMIN_API linmin_status linmin_thresholds(const linmin_threshold_sums *stats, int n_minerals,
                                            float *c_out);
 
+/* Auto-fit of the library (Sec. 2.5, "Estimation of degeneracies"): each
+ * spectrum S_n is fitted by the P - 1 others, S_n = A'.S' + E, without
+ * constraints and with A' >= 0, to show which spectra the others can
+ * mimic.  Unweighted, fp64 on the device, one block per n.
+ *   library   device, P x L (as in linmin_create);
+ *   resid_ls  P x L, row n: the unconstrained residue E (S_n minus its
+ *             projection on the span of the others; unique); may be NULL;
+ *   resid_nn  P x L, row n: the residue under A' >= 0 (unique); may be NULL;
+ *   coef_nn   P x P, row n: the non-negative coefficients of the other
+ *             spectra (0 at n; unique when the others are independent);
+ *             may be NULL;
+ *   rms_ls, rms_nn  P: sqrt(mean_l E^2) of each residue; may be NULL;
+ *   status    int P: 0 converged, 1 active-set iteration cap; may be
+ *             NULL.  A spectrum numerically dependent on the passive ones
+ *             (Cholesky pivot below 1e-14 of its diagonal) is left out.
+ * All output arrays are device memory.  2 <= P <= LINMIN_MAX_P,
+ * P <= L <= LINMIN_MAX_L.  Allocates P * P * L doubles of stream-ordered
+ * scratch; stream: cudaStream_t or NULL; no synchronisation. */
+LINMIN_API linmin_status linmin_autofit(const float *library, int L, int P, float *resid_ls,
+                                        float *resid_nn, float *coef_nn, float *rms_ls,
+                                        float *rms_nn, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
-            "linmin_thresholds")
+            "linmin_thresholds", "linmin_autofit")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -176,6 +176,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_threshold_stats.restype = ctypes.c_int
     lib.linmin_thresholds.argtypes = [ctypes.POINTER(linmin_threshold_sums), ctypes.c_int, P]
     lib.linmin_thresholds.restype = ctypes.c_int
+    lib.linmin_autofit.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P,
+                                   ctypes.c_void_p]
+    lib.linmin_autofit.restype = ctypes.c_int
     return lib
 
 
@@ -370,6 +373,15 @@ def linmin_thresholds(sums: linmin_threshold_sums, n_minerals: int):
     c = np.empty(max(1, n_minerals), dtype=np.float32)
     _check(lib().linmin_thresholds(ctypes.byref(sums), int(n_minerals), _ptr(c)))
     return c[:n_minerals]
+
+
+def linmin_autofit(library, L: int, P: int, resid_ls=None, resid_nn=None, coef_nn=None,
+                   rms_ls=None, rms_nn=None, status=None, stream=None) -> int:
+    """Queue the library auto-fit (device arrays)."""
+    return _check(lib().linmin_autofit(_ptr(library), int(L), int(P), _ptr(resid_ls),
+                                       _ptr(resid_nn), _ptr(coef_nn), _ptr(rms_ls),
+                                       _ptr(rms_nn), _ptr(status, "int32"),
+                                       _stream_ptr(stream)))
 
 
 def _struct_from(buf, cls):
