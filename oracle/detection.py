@@ -9,6 +9,8 @@ CPU-baseline leg may use it; the CUDA library shares no code with it.
   counts, sums, arg-max and, given the truth, the positive / false
   detection counts of Sec. 3.1.
 * ``threshold_sums`` and ``thresholds``: eq. Threshold of Sec. 3.1.
+* ``second_pass``: the second unmixing of Sec. 6 with the detected spectra
+  only, per pixel.
 """
 from __future__ import annotations
 
@@ -121,3 +123,31 @@ def thresholds(x, truth, n_minerals: int) -> np.ndarray:
         if a_pos.size and a_false.size:
             C[i] = 0.5 * (a_pos.mean() - 2.0 * a_pos.std() + a_false.mean() + 6.0 * a_false.std())
     return C
+
+
+def second_pass(S, sigma, X, mask, n_minerals: int) -> dict:
+    """The second pass of Sec. 6: every pixel unmixed again with only the
+    minerals detected in it (bits of ``mask`` below n_minerals) and all the
+    additional spectra (columns >= n_minerals), with the sum-to-one oracle
+    ``oracle.unmix``.  Abundances and uncertainties of the left-out
+    columns are 0.  Returns dict(x, sx (N x P), rms, iters (N))."""
+    from . import unmix
+    S = np.asarray(S, dtype=np.float32)
+    X = np.asarray(X, dtype=np.float32)
+    P = S.shape[0]
+    N = X.shape[0]
+    if not 0 <= n_minerals < P:
+        raise ValueError("0 <= n_minerals < P: the additional spectra are always kept")
+    keep = np.uint64((1 << n_minerals) - 1)
+    m = np.asarray(mask, dtype=np.uint64) & keep
+    out = dict(x=np.zeros((N, P)), sx=np.zeros((N, P)), rms=np.zeros(N),
+               iters=np.zeros(N, np.int32))
+    for key in np.unique(m):
+        rows = np.nonzero(m == key)[0]
+        cols = [i for i in range(n_minerals) if (int(key) >> i) & 1] + list(range(n_minerals, P))
+        r = unmix(S[cols], sigma, X[rows])
+        out["x"][np.ix_(rows, cols)] = r["x"]
+        out["sx"][np.ix_(rows, cols)] = r["sx"]
+        out["rms"][rows] = r["rms"]
+        out["iters"][rows] = r["iters"]
+    return out

@@ -184,3 +184,42 @@ def test_autofit_dependent_extras():
     assert r["rms_ls"].max() < 1e-7
     assert r["rms_nn"][0] > 1e-2 and r["rms_nn"][1] > 1e-2
     assert r["rms_nn"][2] < 1e-7             # 1 = u + 2 * 0.5 (1 - u), weights >= 0
+
+
+# ---------------------------------------------------------- second pass
+def test_second_pass_pins():
+    """(1) A mask holding every mineral is the first pass itself; (2) on
+    noise-free mixtures whose minerals are all in the mask the truth comes
+    back; (3) left-out minerals are 0 and the kept columns satisfy the FCLS
+    optimality conditions (equal g_i + nu on the support, not below
+    elsewhere, g = G x - c)."""
+    import oracle
+    cube = synth.random_instance(51, 40, 64, 10, n_extras=4)
+    nm = 6
+    full = oracle.unmix(cube.S, cube.sigma, cube.X)
+    allm = np.full(cube.N, (1 << nm) - 1, np.uint64)
+    r1 = od.second_pass(cube.S, cube.sigma, cube.X, allm, nm)
+    np.testing.assert_allclose(r1["x"], full["x"], atol=1e-12)
+    np.testing.assert_allclose(r1["sx"], full["sx"], atol=1e-12)
+    # noise-free: X = A_true S with the true minerals in the mask (plus a
+    # random extra bit); the extras are 0 in the truth
+    X0 = (cube.A_true @ cube.S.astype(np.float64)).astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(52))
+    truth = synth.truth_masks(cube.A_true, nm) | (np.uint64(1) << rng.integers(0, nm, cube.N).astype(np.uint64))
+    r2 = od.second_pass(cube.S, cube.sigma, X0, truth, nm)
+    np.testing.assert_allclose(r2["x"], cube.A_true, atol=5e-5)
+    # left-out columns are 0; KKT on the kept ones
+    r3 = od.second_pass(cube.S, cube.sigma, cube.X, truth, nm)
+    G, B = oracle.prep(cube.S, cube.sigma)
+    for n in range(cube.N):
+        kept = [i for i in range(nm) if (int(truth[n]) >> i) & 1] + list(range(nm, cube.P))
+        off = [i for i in range(cube.P) if i not in kept]
+        assert (r3["x"][n, off] == 0).all() and (r3["sx"][n, off] == 0).all()
+        c, _ = oracle.project(B, cube.sigma, cube.X[n])
+        g = G @ r3["x"][n] - c
+        gk = g[kept]
+        xs = r3["x"][n, kept]
+        scale = np.abs(c).max()
+        nu = -gk[xs > 1e-6].mean()
+        assert np.abs(gk[xs > 1e-6] + nu).max() <= 1e-6 * scale
+        assert (gk + nu >= -1e-6 * scale).all()
