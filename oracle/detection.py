@@ -130,7 +130,8 @@ def second_pass(S, sigma, X, mask, n_minerals: int) -> dict:
     minerals detected in it (bits of ``mask`` below n_minerals) and all the
     additional spectra (columns >= n_minerals), with the sum-to-one oracle
     ``oracle.unmix``.  Abundances and uncertainties of the left-out
-    columns are 0.  Returns dict(x, sx (N x P), rms, iters (N))."""
+    columns are 0.  Returns dict(x, sx, lam (N x P: the multipliers of
+    x >= 0, 0 off the kept columns), rms, iters (N))."""
     from . import unmix
     S = np.asarray(S, dtype=np.float32)
     X = np.asarray(X, dtype=np.float32)
@@ -140,7 +141,7 @@ def second_pass(S, sigma, X, mask, n_minerals: int) -> dict:
         raise ValueError("0 <= n_minerals < P: the additional spectra are always kept")
     keep = np.uint64((1 << n_minerals) - 1)
     m = np.asarray(mask, dtype=np.uint64) & keep
-    out = dict(x=np.zeros((N, P)), sx=np.zeros((N, P)), rms=np.zeros(N),
+    out = dict(x=np.zeros((N, P)), sx=np.zeros((N, P)), lam=np.zeros((N, P)), rms=np.zeros(N),
                iters=np.zeros(N, np.int32))
     for key in np.unique(m):
         rows = np.nonzero(m == key)[0]
@@ -148,6 +149,7 @@ def second_pass(S, sigma, X, mask, n_minerals: int) -> dict:
         r = unmix(S[cols], sigma, X[rows])
         out["x"][np.ix_(rows, cols)] = r["x"]
         out["sx"][np.ix_(rows, cols)] = r["sx"]
+        out["lam"][np.ix_(rows, cols)] = r["lam"]
         out["rms"][rows] = r["rms"]
         out["iters"][rows] = r["iters"]
     return out
