@@ -496,6 +496,30 @@ LINMIN_API linmin_status linmin_autofit(const float *library, int L, int P, floa
                                         float *resid_nn, float *coef_nn, float *rms_ls,
                                         float *rms_nn, int *status, void *stream);
 
+/* Second pass (Sec. 6): unmix every pixel again with only the minerals
+ * detected in it and the additional spectra, to sharpen the abundances of
+ * the minerals that are there.
+ *   library   host or device, P x L, the full library (minerals first:
+ *             columns < n_minerals; columns >= n_minerals are additional
+ *             spectra, always kept); its rank is checked as in
+ *             linmin_create (then every subset of its columns is unique too);
+ *   opt       options of the sub-problems (NULL: defaults); the stream is
+ *             opt->cuda_stream;
+ *   cube, sigma, mask (N bit masks, e.g. linmin_detect's output; bits >=
+ *             n_minerals ignored) and the outputs are device memory;
+ *   outputs   as linmin_unmix, N x P with 0 in the left-out columns;
+ *   n_groups  (may be NULL) receives the number of distinct masks.
+ * Pixels are grouped by mask on the host, and each group is unmixed by the
+ * full path with a handle of its own sub-library.  Synchronises the stream
+ * (once for the masks, once at the end).  0 <= n_minerals < P.  Returns
+ * LINMIN_ERR_NOT_CONVERGED when some pixel has iterations < 0. */
+LINMIN_API linmin_status linmin_second_pass(const float *library, int L, int P, int n_minerals,
+                                            const linmin_options *opt, const float *cube,
+                                            long long N, const float *sigma,
+                                            const unsigned long long *mask, float *abundances,
+                                            float *uncertainties, float *residual_rms,
+                                            int *iterations, int *n_groups);
+
 #ifdef __cplusplus
 }
 #endif

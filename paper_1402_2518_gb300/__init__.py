@@ -15,4 +15,5 @@ from .linmin import (EXPORTED, LinminError, Server, Unmixer, library_path, linmi
                      linmin_wait, load,
                      linmin_detect, linmin_extra_spectra, linmin_threshold_stats,
                      linmin_thresholds, linmin_detection, linmin_threshold_sums,
-                     detection_summary, threshold_sums, linmin_autofit)
+                     detection_summary, threshold_sums, linmin_autofit,
+                     linmin_second_pass)

@@ -40,7 +40,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
-            "linmin_thresholds", "linmin_autofit")
+            "linmin_thresholds", "linmin_autofit", "linmin_second_pass")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -179,6 +179,10 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_autofit.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P,
                                    ctypes.c_void_p]
     lib.linmin_autofit.restype = ctypes.c_int
+    lib.linmin_second_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(linmin_options), P, ctypes.c_longlong, P,
+                                       P, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+    lib.linmin_second_pass.restype = ctypes.c_int
     return lib
 
 
@@ -382,6 +386,23 @@ def linmin_autofit(library, L: int, P: int, resid_ls=None, resid_nn=None, coef_n
                                        _ptr(resid_nn), _ptr(coef_nn), _ptr(rms_ls),
                                        _ptr(rms_nn), _ptr(status, "int32"),
                                        _stream_ptr(stream)))
+
+
+def linmin_second_pass(library, L: int, P: int, n_minerals: int, cube, N: int, sigma, mask,
+                       abundances=None, uncertainties=None, residual_rms=None, iterations=None,
+                       opt: linmin_options | None = None) -> tuple[int, int]:
+    """Second pass with the detected spectra (device arrays; synchronous).
+    Returns (status, n_groups); status is LINMIN_OK or
+    LINMIN_ERR_NOT_CONVERGED, other errors raise."""
+    ng = ctypes.c_int(0)
+    st = lib().linmin_second_pass(_ptr(library), int(L), int(P), int(n_minerals),
+                                  ctypes.byref(opt) if opt is not None else None, _ptr(cube),
+                                  int(N), _ptr(sigma), _ptr_any(mask, ("int64", "uint64")),
+                                  _ptr(abundances), _ptr(uncertainties), _ptr(residual_rms),
+                                  _ptr(iterations, "int32"), ctypes.byref(ng))
+    if st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
+        _check(st)
+    return st, ng.value
 
 
 def _struct_from(buf, cls):
