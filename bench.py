@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-cov", action="store_true", help="skip the full-covariance leg")
     ap.add_argument("--no-constraints", action="store_true", help="skip the slo / pos leg")
     ap.add_argument("--no-detection", action="store_true", help="skip the detection leg")
+    ap.add_argument("--second-pass-pixels", type=int, default=65536,
+                    help="pixels of the second-pass leg (0: skip)")
     ap.add_argument("--precision", default="tc", choices=["df", "tc", "bf16"],
                     help="projection: double-float CUDA cores, exact tensor-core slices, bf16")
     ap.add_argument("--serving-cubes", type=int, default=64)
@@ -373,7 +375,8 @@ def run_constraints(pkg, dev, n_pix: int, steps: int):
     return out
 
 
-def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float):
+def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
+                  n_second: int = 65536):
     """Detection products on the unmixed cube: eq. Threshold from the known
     truth (threshold sums kernel), then the per-pixel detection kernel with
     the three conditions of Sec. 5.  Each detection launch is timed alone
@@ -411,6 +414,36 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float):
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
     d = pkg.detection_summary(out)
     nt = int(d["n_true"][:nm].sum())
+    # library auto-fit (Sec. 2.5), one call
+    S = torch.from_numpy(cube.S).to(dev)
+    rl = torch.empty((P, cube.L), device=dev); rn = torch.empty((P, cube.L), device=dev)
+    a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        pkg.linmin_autofit(S, cube.L, P, rl, rn, stream=stream)
+    a0.record(stream)
+    pkg.linmin_autofit(S, cube.L, P, rl, rn, stream=stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    autofit_ms = a0.elapsed_time(a1)
+    # second pass (Sec. 6) on the first pixels, with their detection masks
+    second = None
+    if n_second > 0:
+        n2 = min(N, n_second)
+        X = torch.from_numpy(cube.X[:n2]).to(dev)
+        sg = torch.from_numpy(cube.sigma).to(dev)
+        x2 = torch.empty((n2, P), device=dev); sx2 = torch.empty((n2, P), device=dev)
+        r2 = torch.empty((n2,), device=dev); i2 = torch.empty((n2,), dtype=torch.int32, device=dev)
+        opt = pkg.linmin_default_options()
+        opt.cuda_stream = stream.cuda_stream
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st2, groups = pkg.linmin_second_pass(S, cube.L, P, nm, X, n2, sg, mask[:n2], x2, sx2,
+                                             r2, i2, opt=opt)
+        dt = time.perf_counter() - t0
+        second = {"value": n2 / dt, "unit": "pixels/s", "seconds": dt, "pixels": n2,
+                  "groups": groups, "status": st2,
+                  "note": "host-timed, synchronous call: masks to host, grouping, one "
+                          "sub-library handle and unmix per distinct mask"}
     byts = N * (8 * P + 24)
     gbs = byts / (ms / 1e3) / 1e9
     return {"value": N / (ms / 1e3), "unit": "pixels/s", "ms_per_call": ms,
@@ -422,7 +455,9 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float):
             "thresholds": "eq. Threshold from the truth of the cube (population std)",
             "rms_max": rms_max,
             "positive_detection": int(d["true_pos"][:nm].sum()) / max(nt, 1),
-            "false_detection": int(d["false_pos"][:nm].sum()) / max(N * nm - nt, 1)}
+            "false_detection": int(d["false_pos"][:nm].sum()) / max(N * nm - nt, 1),
+            "autofit_ms": autofit_ms,
+            "second_pass": second}
 
 
 def main():
@@ -515,7 +550,8 @@ def main():
     detection = None
     if not args.no_detection and rank == 0:
         detection = run_detection(pkg, dev, cube, x, sx, rms, it, max(3, args.steps // 2),
-                                  float(measured_peaks().get("hbm_gbs", 6800.0)))
+                                  float(measured_peaks().get("hbm_gbs", 6800.0)),
+                                  args.second_pass_pixels)
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,
