@@ -71,8 +71,7 @@ def parse():
     ap.add_argument("--no-cov", action="store_true", help="skip the full-covariance leg")
     ap.add_argument("--no-constraints", action="store_true", help="skip the slo / pos leg")
     ap.add_argument("--no-detection", action="store_true", help="skip the detection leg")
-    ap.add_argument("--second-pass-pixels", type=int, default=65536,
-                    help="pixels of the second-pass leg (0: skip)")
+    ap.add_argument("--no-second-pass", action="store_true", help="skip the second-pass timing")
     ap.add_argument("--precision", default="tc", choices=["df", "tc", "bf16"],
                     help="projection: double-float CUDA cores, exact tensor-core slices, bf16")
     ap.add_argument("--serving-cubes", type=int, default=64)
@@ -376,7 +375,7 @@ def run_constraints(pkg, dev, n_pix: int, steps: int):
 
 
 def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
-                  n_second: int = 65536):
+                  n_second: bool = True):
     """Detection products on the unmixed cube: eq. Threshold from the known
     truth (threshold sums kernel), then the per-pixel detection kernel with
     the three conditions of Sec. 5.  Each detection launch is timed alone
@@ -425,25 +424,34 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
     a1.record(stream)
     torch.cuda.synchronize()
     autofit_ms = a0.elapsed_time(a1)
-    # second pass (Sec. 6) on the first pixels, with their detection masks
+    # second pass (Sec. 6): every pixel unmixed again with its detected
+    # minerals and the extras (linmin_unmix_masked, K calls timed on the
+    # stream like the main step)
     second = None
-    if n_second > 0:
-        n2 = min(N, n_second)
-        X = torch.from_numpy(cube.X[:n2]).to(dev)
+    if n_second:
+        X = torch.from_numpy(cube.X).to(dev)
         sg = torch.from_numpy(cube.sigma).to(dev)
-        x2 = torch.empty((n2, P), device=dev); sx2 = torch.empty((n2, P), device=dev)
-        r2 = torch.empty((n2,), device=dev); i2 = torch.empty((n2,), dtype=torch.int32, device=dev)
-        opt = pkg.linmin_default_options()
-        opt.cuda_stream = stream.cuda_stream
+        um2 = pkg.Unmixer(S, stream=stream)
+        x2 = torch.empty((N, P), device=dev); sx2 = torch.empty((N, P), device=dev)
+        r2 = torch.empty((N,), device=dev); i2 = torch.empty((N,), dtype=torch.int32, device=dev)
+        for _ in range(2):
+            pkg.linmin_unmix_masked(um2.h, X, N, sg, mask, nm, x2, sx2, r2, i2)
+        st2, nbad2 = um2.wait()
+        b0 = torch.cuda.Event(enable_timing=True); b1 = torch.cuda.Event(enable_timing=True)
+        k2 = max(3, steps // 2)
+        b0.record(stream)
+        for _ in range(k2):
+            pkg.linmin_unmix_masked(um2.h, X, N, sg, mask, nm, x2, sx2, r2, i2)
+        b1.record(stream)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st2, groups = pkg.linmin_second_pass(S, cube.L, P, nm, X, n2, sg, mask[:n2], x2, sx2,
-                                             r2, i2, opt=opt)
-        dt = time.perf_counter() - t0
-        second = {"value": n2 / dt, "unit": "pixels/s", "seconds": dt, "pixels": n2,
-                  "groups": groups, "status": st2,
-                  "note": "host-timed, synchronous call: masks to host, grouping, one "
-                          "sub-library handle and unmix per distinct mask"}
+        ms2 = b0.elapsed_time(b1) / k2
+        um2.close()
+        hm = mask.cpu().numpy()
+        second = {"value": N / (ms2 / 1e3), "unit": "pixels/s", "ms_per_step": ms2,
+                  "pixels": N, "distinct_masks": int(np.unique(hm).size), "status": st2,
+                  "not_converged": nbad2,
+                  "mean_iters": float(i2.to(torch.float64).abs().mean().item()),
+                  "note": "linmin_unmix_masked with the detection masks of this leg"}
     byts = N * (8 * P + 24)
     gbs = byts / (ms / 1e3) / 1e9
     return {"value": N / (ms / 1e3), "unit": "pixels/s", "ms_per_call": ms,
@@ -551,7 +559,7 @@ def main():
     if not args.no_detection and rank == 0:
         detection = run_detection(pkg, dev, cube, x, sx, rms, it, max(3, args.steps // 2),
                                   float(measured_peaks().get("hbm_gbs", 6800.0)),
-                                  args.second_pass_pixels)
+                                  not args.no_second_pass)
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,

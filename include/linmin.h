@@ -496,29 +496,41 @@ LINMIN_API linmin_status linmin_autofit(const float *library, int L, int P, floa
                                         float *resid_nn, float *coef_nn, float *rms_ls,
                                         float *rms_nn, int *status, void *stream);
 
-/* Second pass (Sec. 6): unmix every pixel again with only the minerals
- * detected in it and the additional spectra, to sharpen the abundances of
- * the minerals that are there.
- *   library   host or device, P x L, the full library (minerals first:
- *             columns < n_minerals; columns >= n_minerals are additional
- *             spectra, always kept); its rank is checked as in
- *             linmin_create (then every subset of its columns is unique too);
- *   opt       options of the sub-problems (NULL: defaults); the stream is
- *             opt->cuda_stream;
- *   cube, sigma, mask (N bit masks, e.g. linmin_detect's output; bits >=
- *             n_minerals ignored) and the outputs are device memory;
- *   outputs   as linmin_unmix, N x P with 0 in the left-out columns;
- *   n_groups  (may be NULL) receives the number of distinct masks.
- * Pixels are grouped by mask on the host, and each group is unmixed by the
- * full path with a handle of its own sub-library.  Synchronises the stream
- * (once for the masks, once at the end).  0 <= n_minerals < P.  Returns
- * LINMIN_ERR_NOT_CONVERGED when some pixel has iterations < 0. */
+/* Unmix each pixel with a subset of the library: pixel n uses the
+ * columns j < n_minerals whose bit j is set in mask[n] and every column
+ * j >= n_minerals (the additional spectra), as if it were unmixed with
+ * that sub-library alone; the abundances and uncertainties of its
+ * left-out columns are 0.  This is the second pass of Sec. 6 (mask: the
+ * detections of linmin_detect).  Arguments as linmin_unmix; mask is
+ * device memory (N bit masks, bits >= n_minerals ignored);
+ * 0 <= n_minerals < P (for SLO / POS handles: the caller's P).
+ * The left-out columns are removed by an exact linear penalty on their
+ * projections: c~_j -= K_n with K_n = 2 (max_k |c~_k| + P + 1) + 1, above
+ * any multiplier the sub-problem can give x_j = 0 (c~ and the bound live
+ * in the scaled problem G~ = G / s + 1 1^T, c~ = c / s + 1,
+ * s = trace(G) / P), so the penalised problem has exactly the
+ * sub-problem's minimiser; one extra kernel over the N x P projections. */
+LINMIN_API linmin_status linmin_unmix_masked(linmin_handle h, const float *cube, long long N,
+                                             const float *sigma, const unsigned long long *mask,
+                                             int n_minerals, float *abundances,
+                                             float *uncertainties, float *residual_rms,
+                                             int *iterations);
+
+/* Second pass (Sec. 6) in one call: a handle for the full library
+ * (host or device, P x L, minerals first: columns < n_minerals; rank
+ * checked as in linmin_create, and then every subset of its columns gives
+ * a unique minimiser too), linmin_unmix_masked with the detection masks,
+ * linmin_wait, and the handle freed.
+ *   opt   options (NULL: defaults); the stream is opt->cuda_stream;
+ *   cube, sigma, mask and the outputs are device memory.
+ * Synchronous.  Returns LINMIN_ERR_NOT_CONVERGED when some pixel has
+ * iterations < 0. */
 LINMIN_API linmin_status linmin_second_pass(const float *library, int L, int P, int n_minerals,
                                             const linmin_options *opt, const float *cube,
                                             long long N, const float *sigma,
                                             const unsigned long long *mask, float *abundances,
                                             float *uncertainties, float *residual_rms,
-                                            int *iterations, int *n_groups);
+                                            int *iterations);
 
 #ifdef __cplusplus
 }

@@ -16,4 +16,4 @@ from .linmin import (EXPORTED, LinminError, Server, Unmixer, library_path, linmi
                      linmin_detect, linmin_extra_spectra, linmin_threshold_stats,
                      linmin_thresholds, linmin_detection, linmin_threshold_sums,
                      detection_summary, threshold_sums, linmin_autofit,
-                     linmin_second_pass)
+                     linmin_second_pass, linmin_unmix_masked)

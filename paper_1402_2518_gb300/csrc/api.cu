@@ -424,7 +424,8 @@ static linmin_status load_cov(linmin_ctx *h, const double *cov_inv)
 // linmin_unmix (sigma) and linmin_unmix_cov (cov_inv): exactly one is set
 static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
                                 const double *cov_inv, float *abundances, float *uncertainties,
-                                float *residual_rms, int *iterations)
+                                float *residual_rms, int *iterations,
+                                const unsigned long long *col_mask = nullptr, int n_minerals = 0)
 {
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
     if (N < 0) return fail(h, LINMIN_ERR_INVALID, "N < 0");
@@ -508,6 +509,11 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
                     "tensor-core projection");
         }
     }
+    if (col_mask) {
+        LM_CUDA(h, launch_exclude(col_mask, n_minerals, h->c_hi, h->c_lo, N, P, st),
+                "column-subset penalty");
+        ++proj_launches;
+    }
     mark(h, 2);
 
     IpmArgs ia = ipm_args(h, N);
@@ -577,6 +583,21 @@ linmin_status linmin_unmix(linmin_handle h, const float *cube, long long N, cons
     if (h && N > 0 && !sigma) return fail(h, LINMIN_ERR_INVALID, "sigma is NULL");
     return unmix_impl(h, cube, N, sigma, nullptr, abundances, uncertainties, residual_rms,
                       iterations);
+}
+
+linmin_status linmin_unmix_masked(linmin_handle h, const float *cube, long long N,
+                                  const float *sigma, const unsigned long long *mask,
+                                  int n_minerals, float *abundances, float *uncertainties,
+                                  float *residual_rms, int *iterations)
+{
+    if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
+    if (n_minerals < 0 || n_minerals >= h->user_P)
+        return fail(h, LINMIN_ERR_INVALID, "0 <= n_minerals < P (columns >= n_minerals are always kept)");
+    if (N > 0 && !sigma) return fail(h, LINMIN_ERR_INVALID, "sigma is NULL");
+    if (N > 0 && (!mask || !is_device_ptr(mask)))
+        return fail(h, LINMIN_ERR_INVALID, "mask must be device memory");
+    return unmix_impl(h, cube, N, sigma, nullptr, abundances, uncertainties, residual_rms,
+                      iterations, mask, n_minerals);
 }
 
 linmin_status linmin_unmix_cov(linmin_handle h, const float *cube, long long N,

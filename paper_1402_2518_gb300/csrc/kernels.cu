@@ -224,6 +224,38 @@ __global__ void strip_slack_kernel(const float *__restrict__ xa, const float *__
     }
 }
 
+__global__ void exclude_kernel(const unsigned long long *__restrict__ mask, int n_minerals,
+                               float *c_hi, float *c_lo, long long N, int P)
+{
+    const unsigned long long keep =
+        n_minerals >= 64 ? ~0ull : ((1ull << n_minerals) - 1ull);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long drop = keep & ~mask[n];
+        if (!drop) continue;
+        float* hi = c_hi + n * P;
+        float* lo = c_lo + n * P;
+        float cmax = 0.f;
+        for (int j = 0; j < P; ++j) cmax = fmaxf(cmax, fabsf(hi[j] + lo[j]));
+        const float K = 2.f * (cmax + (float)P + (float)RHO) + 1.f;
+        for (int j = 0; j < n_minerals; ++j) {
+            if (!((drop >> j) & 1ull)) continue;
+            const df r = df_add(df{hi[j], lo[j]}, df_make(-K));
+            hi[j] = r.hi;
+            lo[j] = r.lo;
+        }
+    }
+}
+
+cudaError_t launch_exclude(const unsigned long long *mask, int n_minerals, float *c_hi,
+                           float *c_lo, long long N, int P, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    const long long b = (N + 255) / 256;
+    exclude_kernel<<<(int)(b < 4096 ? b : 4096), 256, 0, st>>>(mask, n_minerals, c_hi, c_lo, N, P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_strip_slack(const float *xa, const float *sxa, long long N, int P, float M,
                                bool bound_check, float *x, float *sx, int *it,
                                unsigned long long *nbad, cudaStream_t st)

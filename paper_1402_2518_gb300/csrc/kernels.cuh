@@ -70,6 +70,15 @@ cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
                                const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st);
 // slo / pos outputs from the slack-augmented internal problem
+// Per-pixel column subsets (the second pass of Sec. 6): for pixel n and
+// each column j < n_minerals whose bit is clear in mask[n], c~_j -= K_n
+// with K_n = 2 (max_k |c~_k| + P + rho) + 1, an exact linear penalty: the
+// multiplier of x_j = 0 in the problem without column j is bounded by
+// 2 (max |c~| + max |G~|) and |G~_ij| <= P + rho, so the penalised
+// problem has the sub-problem's minimiser with x_j = 0 and lambda_j >= 1.
+cudaError_t launch_exclude(const unsigned long long *mask, int n_minerals, float *c_hi,
+                           float *c_lo, long long N, int P, cudaStream_t st);
+
 cudaError_t launch_strip_slack(const float *xa, const float *sxa, long long N, int P, float M,
                                bool bound_check, float *x, float *sx, int *it,
                                unsigned long long *nbad, cudaStream_t st);

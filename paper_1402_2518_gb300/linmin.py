@@ -40,7 +40,8 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_server_last_error", "linmin_server_destroy", "linmin_server_handle_bytes",
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
-            "linmin_thresholds", "linmin_autofit", "linmin_second_pass")
+            "linmin_thresholds", "linmin_autofit", "linmin_second_pass",
+            "linmin_unmix_masked")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -181,8 +182,10 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_autofit.restype = ctypes.c_int
     lib.linmin_second_pass.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(linmin_options), P, ctypes.c_longlong, P,
-                                       P, P, P, P, P, ctypes.POINTER(ctypes.c_int)]
+                                       P, P, P, P, P]
     lib.linmin_second_pass.restype = ctypes.c_int
+    lib.linmin_unmix_masked.argtypes = [H, P, ctypes.c_longlong, P, P, ctypes.c_int, P, P, P, P]
+    lib.linmin_unmix_masked.restype = ctypes.c_int
     return lib
 
 
@@ -390,19 +393,27 @@ def linmin_autofit(library, L: int, P: int, resid_ls=None, resid_nn=None, coef_n
 
 def linmin_second_pass(library, L: int, P: int, n_minerals: int, cube, N: int, sigma, mask,
                        abundances=None, uncertainties=None, residual_rms=None, iterations=None,
-                       opt: linmin_options | None = None) -> tuple[int, int]:
+                       opt: linmin_options | None = None) -> int:
     """Second pass with the detected spectra (device arrays; synchronous).
-    Returns (status, n_groups); status is LINMIN_OK or
-    LINMIN_ERR_NOT_CONVERGED, other errors raise."""
-    ng = ctypes.c_int(0)
+    Returns LINMIN_OK or LINMIN_ERR_NOT_CONVERGED; other errors raise."""
     st = lib().linmin_second_pass(_ptr(library), int(L), int(P), int(n_minerals),
                                   ctypes.byref(opt) if opt is not None else None, _ptr(cube),
                                   int(N), _ptr(sigma), _ptr_any(mask, ("int64", "uint64")),
                                   _ptr(abundances), _ptr(uncertainties), _ptr(residual_rms),
-                                  _ptr(iterations, "int32"), ctypes.byref(ng))
+                                  _ptr(iterations, "int32"))
     if st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
         _check(st)
-    return st, ng.value
+    return st
+
+
+def linmin_unmix_masked(h, cube, N: int, sigma, mask, n_minerals: int, abundances=None,
+                        uncertainties=None, residual_rms=None, iterations=None) -> int:
+    """Unmix with per-pixel library subsets (mask: device bit masks)."""
+    return _check(lib().linmin_unmix_masked(h, _ptr(cube), int(N), _ptr(sigma),
+                                            _ptr_any(mask, ("int64", "uint64")),
+                                            int(n_minerals), _ptr(abundances),
+                                            _ptr(uncertainties), _ptr(residual_rms),
+                                            _ptr(iterations, "int32")), h)
 
 
 def _struct_from(buf, cls):

@@ -86,15 +86,14 @@ def test_second_pass_and_autofit_arguments_rejected_on_host():
     S = np.ones((4, 16), np.float32)
     sp = S.ctypes.data_as(P_)
     inv = linmin.LINMIN_ERR_INVALID
-    ng = ctypes.c_int(-1)
     # n_minerals must leave at least one always-kept column
     assert lib.linmin_second_pass(sp, 16, 4, 4, None, None, 0, None, None, None, None, None,
-                                  None, ctypes.byref(ng)) == inv
-    assert ng.value == 0
+                                  None) == inv
     assert lib.linmin_second_pass(sp, 16, 0, 0, None, None, 0, None, None, None, None, None,
-                                  None, None) == inv
+                                  None) == inv
     assert lib.linmin_second_pass(None, 16, 4, 2, None, None, 0, None, None, None, None, None,
-                                  None, None) == inv
+                                  None) == inv
+    assert lib.linmin_unmix_masked(None, None, 0, None, None, 0, None, None, None, None) == inv
     assert lib.linmin_autofit(sp, 16, 1, None, None, None, None, None, None, None) == inv
     assert lib.linmin_autofit(sp, 3, 4, None, None, None, None, None, None, None) == inv
     assert lib.linmin_autofit(None, 16, 4, None, None, None, None, None, None, None) == inv

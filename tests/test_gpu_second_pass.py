@@ -35,10 +35,10 @@ def run(pkg, S, X, sigma, mask, nm):
     rms = torch.full((max(N, 1),), np.nan, device=DEV)
     it = torch.zeros((max(N, 1),), dtype=torch.int32, device=DEV)
     dummy = torch.zeros((1,), dtype=torch.int64, device=DEV)
-    st, ng = pkg.linmin_second_pass(_d(S), S.shape[1], P, nm, _d(X) if N else x, N, _d(sigma),
-                                    _d(mask) if N else dummy, x, sx, rms, it)
+    st = pkg.linmin_second_pass(_d(S), S.shape[1], P, nm, _d(X) if N else x, N, _d(sigma),
+                                _d(mask) if N else dummy, x, sx, rms, it)
     torch.cuda.synchronize()
-    return st, ng, [t[:N].cpu().numpy().astype(np.float64) for t in (x, sx, rms)] + [it[:N].cpu().numpy()]
+    return st, [t[:N].cpu().numpy().astype(np.float64) for t in (x, sx, rms)] + [it[:N].cpu().numpy()]
 
 
 def check(got, ref, mask, nm, S, sigma):
@@ -78,9 +78,9 @@ def test_second_pass_on_detections(pkg):
     det = od.detect(first["x"].astype(np.float32), first["sx"].astype(np.float32),
                     first["rms"].astype(np.float32), first["iters"], truth, C,
                     float(2 * cube.sigma.mean()), nm)
-    st, ng, got = run(pkg, cube.S, cube.X, cube.sigma, det["mask"], nm)
+    st, got = run(pkg, cube.S, cube.X, cube.sigma, det["mask"], nm)
     ref = od.second_pass(cube.S, cube.sigma, cube.X, det["mask"], nm)
-    assert st == 0 and ng == len(np.unique(det["mask"]))
+    assert st == 0
     check(got, ref, det["mask"], nm, cube.S, cube.sigma)
 
 
@@ -89,9 +89,9 @@ def test_second_pass_true_minerals_sharpen(pkg):
     abundances closer to the truth than the first (the claim of Sec. 6)."""
     cube, truth = synth.surface_mixtures()
     nm = 32
-    st, ng, got = run(pkg, cube.S, cube.X, cube.sigma, truth, nm)
+    st, got = run(pkg, cube.S, cube.X, cube.sigma, truth, nm)
     ref = od.second_pass(cube.S, cube.sigma, cube.X, truth, nm)
-    assert st == 0 and ng == 32
+    assert st == 0
     check(got, ref, truth, nm, cube.S, cube.sigma)
     first = oracle.unmix(cube.S, cube.sigma, cube.X)
     pres = cube.A_true[:, :nm] > 0
@@ -108,14 +108,40 @@ def test_second_pass_random_masks(pkg):
     masks = rng.integers(0, 1 << 5, cube.N).astype(np.uint64) << np.uint64(3)   # 32 groups
     masks[rng.random(cube.N) < 0.1] = 0                                      # extras only
     masks[:7] = np.uint64((1 << nm) - 1) | np.uint64(1 << 40)                # high bits ignored
-    st, ng, got = run(pkg, cube.S, cube.X, cube.sigma, masks, nm)
+    st, got = run(pkg, cube.S, cube.X, cube.sigma, masks, nm)
     ref = od.second_pass(cube.S, cube.sigma, cube.X, masks, nm)
     assert st == 0
-    assert ng == len(np.unique(masks & np.uint64((1 << nm) - 1)))
     check(got, ref, masks, nm, cube.S, cube.sigma)
 
 
 def test_second_pass_empty(pkg):
     cube = synth.random_instance(63, 10, 64, 8, n_extras=4)
-    st, ng, got = run(pkg, cube.S, cube.X[:0], cube.sigma, np.zeros(0, np.uint64), 4)
-    assert st == 0 and ng == 0
+    st, got = run(pkg, cube.S, cube.X[:0], cube.sigma, np.zeros(0, np.uint64), 4)
+    assert st == 0
+
+
+@pytest.mark.parametrize("constraint", [1, 2])
+def test_masked_unmix_constraint_sets(pkg, constraint):
+    """The per-pixel subsets under slo / pos equal the oracle's constraint
+    sets on each pixel's sub-library."""
+    cube = synth.random_instance(64, 700, 128, 14, n_extras=0)
+    nm = 10
+    rng = np.random.Generator(np.random.PCG64(65))
+    masks = rng.integers(1, 1 << nm, cube.N).astype(np.uint64)
+    um = pkg.Unmixer(_d(cube.S), constraint=constraint)
+    N, P = cube.N, cube.P
+    x = torch.empty((N, P), device=DEV); sx = torch.empty((N, P), device=DEV)
+    rms = torch.empty((N,), device=DEV); it = torch.empty((N,), dtype=torch.int32, device=DEV)
+    pkg.linmin_unmix_masked(um.h, _d(cube.X), N, _d(cube.sigma), _d(masks), nm, x, sx, rms, it)
+    st, nbad = um.wait()
+    um.close()
+    assert st == 0
+    name = {1: "slo", 2: "pos"}[constraint]
+    gx = x.cpu().numpy()
+    for key in np.unique(masks)[:25]:
+        rows = np.nonzero(masks == key)[0]
+        cols = [i for i in range(nm) if (int(key) >> i) & 1] + list(range(nm, P))
+        ref = oracle.unmix_constraint(cube.S[cols], cube.sigma, cube.X[rows], name)
+        assert np.abs(gx[np.ix_(rows, cols)] - ref["x"]).max() <= 1e-4
+        off = [i for i in range(P) if i not in cols]
+        assert (gx[np.ix_(rows, off)] == 0).all()
