@@ -2,13 +2,14 @@
 // the per-pixel detection conditions (Sec. 5), and the statistics of the
 // per-mineral threshold (Sec. 3.1, eq. Threshold).
 //
-// Both device kernels read the N x P abundance array once: a block stages
-// a tile of DT pixels (rows padded to P + 1 floats, so that column reads
-// are conflict-free) with coalesced loads, evaluates one pixel per thread
-// (the detection mask), then one mineral per thread walks the tile's
-// pixels and keeps its sums in registers; one atomic per mineral and block
-// at the end.  Memory bound: 4P (x) + 4P (sx) + 16 bytes read and 8 bytes
-// written per pixel.
+// Both device kernels stream the N x P abundance array once with the lane
+// of a warp as the mineral: a warp walks a contiguous range of pixels,
+// lane i reads x[n, i] (and x[n, i + 32]; a pixel's row is one coalesced
+// read), decides mineral i, and a warp ballot gives the pixel's detection
+// mask; each lane keeps its mineral's counts, sum and arg-max in registers
+// over the whole range, with one atomic per mineral and warp at the end.
+// Memory bound: 4P (x) + 4P (sx) + 16 bytes read and 8 bytes written per
+// pixel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,8 +22,10 @@
 
 namespace {
 
-constexpr int DT = 64;            // pixels per tile = threads per block
-constexpr int DMAX_BLOCKS = 152 * 16;
+constexpr int DTH = 256;                 // threads per block
+constexpr int DBLOCKS = 152 * 4;         // blocks (8 warps each)
+constexpr int DU = 4;                    // pixels per warp step (loads in flight)
+constexpr unsigned FULLM = 0xffffffffu;
 
 struct DetectArgs {
     const float *x, *sx, *rms;
@@ -36,18 +39,6 @@ struct DetectArgs {
     float xmin[LINMIN_MAX_P];
 };
 
-// Stage rows [n0, n0 + rows) of a N x P float array into s (stride P + 1).
-__device__ __forceinline__ void stage_rows(float *s, const float *g, long long n0, int rows,
-                                           int P)
-{
-    const long long base = n0 * P;
-    const int ne = rows * P;
-    for (int e = threadIdx.x; e < ne; e += DT) {
-        const int r = e / P, c = e - r * P;
-        s[r * (P + 1) + c] = __ldg(g + base + e);
-    }
-}
-
 // Order key of a detected abundance (x > 0): larger x first, then the
 // smaller pixel index.
 __device__ __forceinline__ unsigned long long max_key(float x, long long n)
@@ -56,81 +47,100 @@ __device__ __forceinline__ unsigned long long max_key(float x, long long n)
            (unsigned long long)(0xffffffffu - (unsigned)n);
 }
 
-__global__ void __launch_bounds__(DT) detect_kernel(DetectArgs a)
+// Contiguous pixel range of this warp.
+__device__ __forceinline__ void warp_range(long long N, long long &n0, long long &n1)
 {
-    extern __shared__ float sm[];
-    const int P = a.P, ld = P + 1;
-    float *xs = sm;
-    float *ss = xs + DT * ld;
-    unsigned long long *ms = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(ss + DT * ld) + 7) & ~(uintptr_t)7);
-    unsigned long long *ts = ms + DT;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long per = (N + nw - 1) / nw;
+    n0 = w * per;
+    n1 = n0 + per < N ? n0 + per : N;
+}
 
-    const int i = threadIdx.x;               // mineral of the column pass
-    const bool cols = a.out != nullptr && i < a.nm;
+struct MinAcc {
     long long cnt = 0, ntr = 0, tp = 0, fp = 0;
     double xsum = 0.0;
     unsigned long long key = 0;
+};
 
-    const long long tiles = (a.N + DT - 1) / DT;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const long long n0 = t * DT;
-        const long long rem = a.N - n0;
-        const int rows = rem < DT ? (int)rem : DT;
-        stage_rows(xs, a.x, n0, rows, P);
-        if (a.sx) stage_rows(ss, a.sx, n0, rows, P);
-        __syncthreads();
-        // one pixel per thread: the detection mask
-        if (threadIdx.x < rows) {
-            const int r = threadIdx.x;
-            const long long n = n0 + r;
-            bool ok = true;
-            if (a.rms) ok = __ldg(a.rms + n) < a.rms_max;
-            if (a.it) ok = ok && __ldg(a.it + n) >= 0;
-            unsigned long long m = 0;
-            if (ok) {
-                for (int j = 0; j < a.nm; ++j) {
-                    const float xv = xs[r * ld + j];
-                    bool d = xv > a.xmin[j];
-                    if (a.sx) d = d && ss[r * ld + j] < xv;
-                    m |= (unsigned long long)d << j;
+__global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int P = a.P, nm = a.nm;
+    const int i0 = lane, i1 = lane + 32;
+    const bool has0 = i0 < nm, has1 = i1 < nm;
+    const float xm0 = has0 ? a.xmin[i0] : 0.f, xm1 = has1 ? a.xmin[i1] : 0.f;
+    MinAcc m0, m1;
+    long long n0, n1;
+    warp_range(a.N, n0, n1);
+    for (long long nb = n0; nb < n1; nb += DU) {
+        float xv0[DU], xv1[DU], sv0[DU], sv1[DU];
+        bool ok[DU];
+        unsigned long long tr[DU];
+#pragma unroll
+        for (int u = 0; u < DU; ++u) {
+            const long long n = nb + u;
+            const bool in = n < n1;
+            const float *xr = a.x + n * P;
+            xv0[u] = in && has0 ? __ldg(xr + i0) : 0.f;
+            xv1[u] = in && has1 ? __ldg(xr + i1) : 0.f;
+            if (a.sx) {
+                const float *sr = a.sx + n * P;
+                sv0[u] = in && has0 ? __ldg(sr + i0) : 0.f;
+                sv1[u] = in && has1 ? __ldg(sr + i1) : 0.f;
+            }
+            bool o = in;
+            if (in && a.rms) o = __ldg(a.rms + n) < a.rms_max;
+            if (in && a.it) o = o && __ldg(a.it + n) >= 0;
+            ok[u] = o;
+            tr[u] = in && a.truth ? __ldg(a.truth + n) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < DU; ++u) {
+            const long long n = nb + u;
+            bool d0 = ok[u] && has0 && xv0[u] > xm0;
+            bool d1 = ok[u] && has1 && xv1[u] > xm1;
+            if (a.sx) {
+                d0 = d0 && sv0[u] < xv0[u];
+                d1 = d1 && sv1[u] < xv1[u];
+            }
+            const unsigned b0 = __ballot_sync(FULLM, d0), b1 = __ballot_sync(FULLM, d1);
+            if (n >= n1) continue;
+            if (lane == 0 && a.mask) a.mask[n] = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
+            const bool t0 = (tr[u] >> i0) & 1ull, t1 = i1 < 64 && ((tr[u] >> i1) & 1ull);
+            if (has0) {
+                m0.ntr += t0; m0.tp += d0 && t0; m0.fp += d0 && !t0;
+                if (d0) {
+                    ++m0.cnt; m0.xsum += (double)xv0[u];
+                    const unsigned long long k = max_key(xv0[u], n);
+                    m0.key = k > m0.key ? k : m0.key;
                 }
             }
-            ms[r] = m;
-            ts[r] = a.truth ? __ldg(a.truth + n) : 0ull;
-            if (a.mask) a.mask[n] = m;
-        }
-        __syncthreads();
-        // one mineral per thread: counts, sum, arg-max, rates
-        if (cols) {
-            for (int r = 0; r < rows; ++r) {
-                const bool d = (ms[r] >> i) & 1ull;
-                const bool tr = (ts[r] >> i) & 1ull;
-                ntr += tr;
-                tp += d && tr;
-                fp += d && !tr;
-                if (d) {
-                    const float xv = xs[r * ld + i];
-                    ++cnt;
-                    xsum += (double)xv;
-                    const unsigned long long k = max_key(xv, n0 + r);
-                    key = k > key ? k : key;
+            if (has1) {
+                m1.ntr += t1; m1.tp += d1 && t1; m1.fp += d1 && !t1;
+                if (d1) {
+                    ++m1.cnt; m1.xsum += (double)xv1[u];
+                    const unsigned long long k = max_key(xv1[u], n);
+                    m1.key = k > m1.key ? k : m1.key;
                 }
             }
         }
-        __syncthreads();
     }
-    if (cols) {
-        linmin_detection *o = a.out;
-        if (cnt) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&o->count[i]), (unsigned long long)cnt);
-            atomicAdd(&o->xsum[i], xsum);
-            atomicMax(&o->key[i], key);
+    if (!a.out) return;
+    linmin_detection *o = a.out;
+    for (int h = 0; h < 2; ++h) {
+        const int i = h ? i1 : i0;
+        const MinAcc &m = h ? m1 : m0;
+        if (i >= nm) continue;
+        if (m.cnt) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&o->count[i]), (unsigned long long)m.cnt);
+            atomicAdd(&o->xsum[i], m.xsum);
+            atomicMax(&o->key[i], m.key);
         }
         if (a.truth) {
-            if (ntr) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_true[i]), (unsigned long long)ntr);
-            if (tp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->true_pos[i]), (unsigned long long)tp);
-            if (fp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->false_pos[i]), (unsigned long long)fp);
+            if (m.ntr) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_true[i]), (unsigned long long)m.ntr);
+            if (m.tp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->true_pos[i]), (unsigned long long)m.tp);
+            if (m.fp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->false_pos[i]), (unsigned long long)m.fp);
         }
     }
 }
@@ -157,51 +167,42 @@ struct StatsArgs {
     linmin_threshold_sums *out;
 };
 
-__global__ void __launch_bounds__(DT) threshold_stats_kernel(StatsArgs a)
+__global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
 {
-    extern __shared__ float sm[];
-    const int P = a.P, ld = P + 1;
-    float *xs = sm;
-    unsigned long long *ts = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(xs + DT * ld) + 7) & ~(uintptr_t)7);
-    const int i = threadIdx.x;
-    long long np = 0, nn = 0;
-    double sp = 0.0, qp = 0.0, sn = 0.0, qn = 0.0;
-    const long long tiles = (a.N + DT - 1) / DT;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const long long n0 = t * DT;
-        const long long rem = a.N - n0;
-        const int rows = rem < DT ? (int)rem : DT;
-        stage_rows(xs, a.x, n0, rows, P);
-        if (threadIdx.x < rows) ts[threadIdx.x] = __ldg(a.truth + n0 + threadIdx.x);
-        __syncthreads();
-        if (i < a.nm) {
-            for (int r = 0; r < rows; ++r) {
-                const double v = (double)xs[r * ld + i];
-                if ((ts[r] >> i) & 1ull) { ++np; sp += v; qp += v * v; }
-                else                     { ++nn; sn += v; qn += v * v; }
-            }
+    const int lane = threadIdx.x & 31;
+    const int P = a.P, nm = a.nm;
+    long long np[2] = {0, 0}, nn[2] = {0, 0};
+    double sp[2] = {0.0, 0.0}, qp[2] = {0.0, 0.0}, sn[2] = {0.0, 0.0}, qn[2] = {0.0, 0.0};
+    long long n0, n1;
+    warp_range(a.N, n0, n1);
+    for (long long n = n0; n < n1; ++n) {
+        const unsigned long long t = __ldg(a.truth + n);
+        const float *xr = a.x + n * P;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = lane + 32 * h;
+            if (i >= nm) continue;
+            const double v = (double)__ldg(xr + i);
+            if ((t >> i) & 1ull) { ++np[h]; sp[h] += v; qp[h] += v * v; }
+            else                 { ++nn[h]; sn[h] += v; qn[h] += v * v; }
         }
-        __syncthreads();
     }
-    if (i < a.nm) {
-        linmin_threshold_sums *o = a.out;
-        if (np) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)np);
-        if (nn) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)nn);
-        atomicAdd(&o->sum_pos[i], sp);
-        atomicAdd(&o->sumsq_pos[i], qp);
-        atomicAdd(&o->sum_neg[i], sn);
-        atomicAdd(&o->sumsq_neg[i], qn);
+    linmin_threshold_sums *o = a.out;
+    for (int h = 0; h < 2; ++h) {
+        const int i = lane + 32 * h;
+        if (i >= nm) continue;
+        if (np[h]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)np[h]);
+        if (nn[h]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)nn[h]);
+        if (np[h]) { atomicAdd(&o->sum_pos[i], sp[h]); atomicAdd(&o->sumsq_pos[i], qp[h]); }
+        if (nn[h]) { atomicAdd(&o->sum_neg[i], sn[h]); atomicAdd(&o->sumsq_neg[i], qn[h]); }
     }
 }
 
-size_t detect_smem(int P) { return (size_t)2 * DT * (P + 1) * sizeof(float) + 8 + 2 * DT * 8; }
-size_t stats_smem(int P) { return (size_t)DT * (P + 1) * sizeof(float) + 8 + DT * 8; }
-
 int grid_for(long long N)
 {
-    const long long tiles = (N + DT - 1) / DT;
-    return (int)std::max<long long>(1, std::min<long long>(tiles, DMAX_BLOCKS));
+    const long long warps = (N + 15) / 16;            // at least 16 pixels per warp
+    const long long b = (warps + DTH / 32 - 1) / (DTH / 32);
+    return (int)std::max<long long>(1, std::min<long long>(b, DBLOCKS));
 }
 
 linmin_status err(linmin_status st, const std::string &m)
@@ -294,8 +295,7 @@ linmin_status linmin_detect(const float *x, const float *sx, const float *rms,
         a.N = N; a.P = P; a.nm = n_minerals; a.rms_max = rms_max; a.mask = mask;
         a.out = out;
         for (int i = 0; i < LINMIN_MAX_P; ++i) a.xmin[i] = i < n_minerals ? x_min[i] : 0.f;
-        const size_t smem = detect_smem(P);
-        detect_kernel<<<grid_for(N), DT, smem, s>>>(a);
+        detect_kernel<<<grid_for(N), DTH, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "linmin_detect: launch");
     }
     if (out) {
@@ -322,7 +322,7 @@ linmin_status linmin_threshold_stats(const float *x, const unsigned long long *t
     if (e != cudaSuccess) return cuda_err(e, "linmin_threshold_stats: memset");
     if (N > 0 && n_minerals > 0) {
         StatsArgs a{x, truth, N, P, n_minerals, out};
-        threshold_stats_kernel<<<grid_for(N), DT, stats_smem(P), s>>>(a);
+        threshold_stats_kernel<<<grid_for(N), DTH, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "linmin_threshold_stats: launch");
     }
     return LINMIN_OK;
