@@ -741,6 +741,8 @@ crossover_group_kernel(const CrossArgs a)
     constexpr int KS = C::KS;
     extern __shared__ __align__(16) float sgm[];
     const int P = a.P;
+    const unsigned long long n_work = *a.len_in;
+    if ((unsigned long long)blockIdx.x * C::GROUPS >= n_work) return;   // no pixel for this block
     float *sGh = sgm, *sGl = sgm + P * P;
     for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
         const int i = e / P, j = e % P;
@@ -754,262 +756,267 @@ crossover_group_kernel(const CrossArgs a)
     int *sidx = reinterpret_cast<int *>(xl + KMAX);
     __syncthreads();
     const df zero = df_make(0.f);
-    const unsigned long long n_work = *a.len_in;
     const long long stride = (long long)gridDim.x * C::GROUPS;
     for (long long slot = (long long)blockIdx.x * C::GROUPS + grp; slot < (long long)n_work;
          slot += stride) {
         const long long n = a.list_in[slot];
         const size_t base = (size_t)n * P;
-        const unsigned long long m = a.mask[n];
-        const int k = __popcll(m);
-        for (int i = t; i < P; i += XG)
-            if ((m >> i) & 1ULL) sidx[__popcll(m & ((1ULL << i) - 1ULL))] = i;
-        __syncwarp(gmask);
-        // L = G~_SS on the own rows; right-hand sides 1 and c~_S
-        df au[KS], av[KS], uu[KS], vv[KS];
-#pragma unroll
-        for (int s = 0; s < KS; ++s) {
-            const int r = s * XG + t;
-            au[s] = av[s] = uu[s] = vv[s] = zero;
-            if (r < k) {
-                const int gr = sidx[r];
-                for (int j = 0; j <= r; ++j) {
-                    const int gj = sidx[j];
-                    Lh[pk(r, j)] = sGh[gr * P + gj];
-                    Ll[pk(r, j)] = sGl[gr * P + gj];
-                }
-                au[s] = df_make(1.f);
-                av[s] = df{a.c_hi[base + gr], a.c_lo[base + gr]};
-            }
-        }
-        __syncwarp(gmask);
-        // right-looking Cholesky; the diagonal keeps 1/L_cc
-        bool ok = true;
-        for (int c = 0; c < k; ++c) {
-            df d = df{Lh[pk(c, c)], Ll[pk(c, c)]};
-            if (!(d.hi > 0.f)) { ok = false; d = df_make(1e-30f); }
-            const df rl = df_rsqrt(d);
-            df uc = zero, vc = zero, lrc[KS];
+        unsigned long long m = a.mask[n];
+        // up to max_solves support solves for this pixel: each failed KKT
+        // check flips one coordinate and solves again on the new support
+        for (int solve = 0;; ++solve) {
+            const bool can_flip = solve + 1 < a.max_solves;
+            const int k = __popcll(m);
+            for (int i = t; i < P; i += XG)
+                if ((m >> i) & 1ULL) sidx[__popcll(m & ((1ULL << i) - 1ULL))] = i;
+            __syncwarp(gmask);
+            // L = G~_SS on the own rows; right-hand sides 1 and c~_S
+            df au[KS], av[KS], uu[KS], vv[KS];
 #pragma unroll
             for (int s = 0; s < KS; ++s) {
                 const int r = s * XG + t;
-                lrc[s] = zero;
-                if (r > c && r < k) {
-                    lrc[s] = df_mul(df{Lh[pk(r, c)], Ll[pk(r, c)]}, rl);
-                    Lh[pk(r, c)] = lrc[s].hi;
-                    Ll[pk(r, c)] = lrc[s].lo;
-                }
-                if (r == c) {
-                    uc = df_mul(au[s], rl);
-                    vc = df_mul(av[s], rl);
-                    uu[s] = uc;
-                    vv[s] = vc;
-                    Lh[pk(c, c)] = rl.hi;
-                    Ll[pk(c, c)] = rl.lo;
+                au[s] = av[s] = uu[s] = vv[s] = zero;
+                if (r < k) {
+                    const int gr = sidx[r];
+                    for (int j = 0; j <= r; ++j) {
+                        const int gj = sidx[j];
+                        Lh[pk(r, j)] = sGh[gr * P + gj];
+                        Ll[pk(r, j)] = sGl[gr * P + gj];
+                    }
+                    au[s] = df_make(1.f);
+                    av[s] = df{a.c_hi[base + gr], a.c_lo[base + gr]};
                 }
             }
-            uc = shfl_df(gmask, uc, c % XG);
-            vc = shfl_df(gmask, vc, c % XG);
-            __syncwarp(gmask);                       // column c of L stored
-#pragma unroll
-            for (int s = 0; s < KS; ++s) {
-                const int r = s * XG + t;
-                if (r > c && r < k) {
-                    au[s] = df_fms(au[s], lrc[s], uc);
-                    av[s] = df_fms(av[s], lrc[s], vc);
-                }
-            }
-            // trailing update L_rj -= L_rc L_jc (c < j <= r): the lane's rows
-            // advance together (independent chains), L_jc read once per j
-            for (int j = c + 1; j < k; ++j) {
-                const df ljc = df{Lh[pk(j, c)], Ll[pk(j, c)]};
+            __syncwarp(gmask);
+            // right-looking Cholesky; the diagonal keeps 1/L_cc
+            bool ok = true;
+            for (int c = 0; c < k; ++c) {
+                df d = df{Lh[pk(c, c)], Ll[pk(c, c)]};
+                if (!(d.hi > 0.f)) { ok = false; d = df_make(1e-30f); }
+                const df rl = df_rsqrt(d);
+                df uc = zero, vc = zero, lrc[KS];
 #pragma unroll
                 for (int s = 0; s < KS; ++s) {
                     const int r = s * XG + t;
-                    if (r >= j && r < k) {
-                        const df v = df_fms(df{Lh[pk(r, j)], Ll[pk(r, j)]}, lrc[s], ljc);
-                        Lh[pk(r, j)] = v.hi;
-                        Ll[pk(r, j)] = v.lo;
+                    lrc[s] = zero;
+                    if (r > c && r < k) {
+                        lrc[s] = df_mul(df{Lh[pk(r, c)], Ll[pk(r, c)]}, rl);
+                        Lh[pk(r, c)] = lrc[s].hi;
+                        Ll[pk(r, c)] = lrc[s].lo;
+                    }
+                    if (r == c) {
+                        uc = df_mul(au[s], rl);
+                        vc = df_mul(av[s], rl);
+                        uu[s] = uc;
+                        vv[s] = vc;
+                        Lh[pk(c, c)] = rl.hi;
+                        Ll[pk(c, c)] = rl.lo;
                     }
                 }
-            }
-            __syncwarp(gmask);                       // trailing block updated
-        }
-        // nu from the bordered system
-        df a11 = zero, a1b = zero;
+                uc = shfl_df(gmask, uc, c % XG);
+                vc = shfl_df(gmask, vc, c % XG);
+                __syncwarp(gmask);                       // column c of L stored
 #pragma unroll
-        for (int s = 0; s < KS; ++s)
-            if (s * XG + t < k) {
-                a11 = df_add(a11, df_mul(uu[s], uu[s]));
-                a1b = df_add(a1b, df_mul(uu[s], vv[s]));
-            }
-        a11 = group_sum_df(gmask, a11);
-        a1b = group_sum_df(gmask, a1b);
-        const df nu = df_div(df_sub(a1b, df_make(1.f)), a11);
-        // back solve: xs = L^-T (v - nu u), ub = L^-T u (= G~_SS^-1 1)
-        df ax[KS], ab[KS], xs[KS], ub[KS];
+                for (int s = 0; s < KS; ++s) {
+                    const int r = s * XG + t;
+                    if (r > c && r < k) {
+                        au[s] = df_fms(au[s], lrc[s], uc);
+                        av[s] = df_fms(av[s], lrc[s], vc);
+                    }
+                }
+                // trailing update L_rj -= L_rc L_jc (c < j <= r): the lane's rows
+                // advance together (independent chains), L_jc read once per j
+                for (int j = c + 1; j < k; ++j) {
+                    const df ljc = df{Lh[pk(j, c)], Ll[pk(j, c)]};
 #pragma unroll
-        for (int s = 0; s < KS; ++s) {
-            ax[s] = df_fms(vv[s], nu, uu[s]);
-            ab[s] = uu[s];
-            xs[s] = ub[s] = zero;
-        }
-        for (int r = k - 1; r >= 0; --r) {
-            df xr = zero, ur = zero;
+                    for (int s = 0; s < KS; ++s) {
+                        const int r = s * XG + t;
+                        if (r >= j && r < k) {
+                            const df v = df_fms(df{Lh[pk(r, j)], Ll[pk(r, j)]}, lrc[s], ljc);
+                            Lh[pk(r, j)] = v.hi;
+                            Ll[pk(r, j)] = v.lo;
+                        }
+                    }
+                }
+                __syncwarp(gmask);                       // trailing block updated
+            }
+            // nu from the bordered system
+            df a11 = zero, a1b = zero;
 #pragma unroll
             for (int s = 0; s < KS; ++s)
-                if (s * XG + t == r) {
-                    const df rlr = df{Lh[pk(r, r)], Ll[pk(r, r)]};
-                    xr = df_mul(ax[s], rlr);
-                    ur = df_mul(ab[s], rlr);
-                    xs[s] = xr;
-                    ub[s] = ur;
+                if (s * XG + t < k) {
+                    a11 = df_add(a11, df_mul(uu[s], uu[s]));
+                    a1b = df_add(a1b, df_mul(uu[s], vv[s]));
                 }
-            xr = shfl_df(gmask, xr, r % XG);
-            ur = shfl_df(gmask, ur, r % XG);
+            a11 = group_sum_df(gmask, a11);
+            a1b = group_sum_df(gmask, a1b);
+            const df nu = df_div(df_sub(a1b, df_make(1.f)), a11);
+            // back solve: xs = L^-T (v - nu u), ub = L^-T u (= G~_SS^-1 1)
+            df ax[KS], ab[KS], xs[KS], ub[KS];
 #pragma unroll
             for (int s = 0; s < KS; ++s) {
-                const int q = s * XG + t;
-                if (q < r) {
-                    const df lrq = df{Lh[pk(r, q)], Ll[pk(r, q)]};
-                    ax[s] = df_fms(ax[s], lrq, xr);
-                    ab[s] = df_fms(ab[s], lrq, ur);
-                }
+                ax[s] = df_fms(vv[s], nu, uu[s]);
+                ab[s] = uu[s];
+                xs[s] = ub[s] = zero;
             }
-        }
-        // decision
-        int flip = -1;
-        df xsum = zero;
-        if (ok) {
-            float xmin = (float)-a.tol_x;
-            int fr = -1;
+            for (int r = k - 1; r >= 0; --r) {
+                df xr = zero, ur = zero;
 #pragma unroll
-            for (int s = 0; s < KS; ++s) {
-                const int r = s * XG + t;
-                if (r < k) {
-                    if (xs[s].hi < xmin) { xmin = xs[s].hi; fr = r; }
-                    if (xs[s].hi > 0.f) xsum = df_add(xsum, xs[s]);
+                for (int s = 0; s < KS; ++s)
+                    if (s * XG + t == r) {
+                        const df rlr = df{Lh[pk(r, r)], Ll[pk(r, r)]};
+                        xr = df_mul(ax[s], rlr);
+                        ur = df_mul(ab[s], rlr);
+                        xs[s] = xr;
+                        ub[s] = ur;
+                    }
+                xr = shfl_df(gmask, xr, r % XG);
+                ur = shfl_df(gmask, ur, r % XG);
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    const int q = s * XG + t;
+                    if (q < r) {
+                        const df lrq = df{Lh[pk(r, q)], Ll[pk(r, q)]};
+                        ax[s] = df_fms(ax[s], lrq, xr);
+                        ab[s] = df_fms(ab[s], lrq, ur);
+                    }
                 }
             }
-            group_argmin(gmask, xmin, fr);
-            xsum = group_sum_df(gmask, xsum);
-            if (fr >= 0) flip = (k == 1) ? -2 : sidx[fr];
-            if (flip == -1) {
-                // most negative multiplier off S, coordinates spread over the lanes
+            // decision
+            int flip = -1;
+            df xsum = zero;
+            if (ok) {
+                float xmin = (float)-a.tol_x;
+                int fr = -1;
 #pragma unroll
                 for (int s = 0; s < KS; ++s) {
                     const int r = s * XG + t;
-                    if (r < k) { xh[r] = xs[s].hi; xl[r] = xs[s].lo; }
-                }
-                __syncwarp(gmask);
-                float lmin = (float)-a.tol_g;
-                int fi = -1;
-                for (int i = t; i < P; i += XG) {
-                    if ((m >> i) & 1ULL) continue;
-                    dot2 g;
-                    for (int q = 0; q < k; ++q) {
-                        const float gh = sGh[i * P + sidx[q]], gl = sGl[i * P + sidx[q]];
-                        g.add_prod(gh, xh[q]);
-                        g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+                    if (r < k) {
+                        if (xs[s].hi < xmin) { xmin = xs[s].hi; fr = r; }
+                        if (xs[s].hi > 0.f) xsum = df_add(xsum, xs[s]);
                     }
-                    g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
-                    g.add_df(nu);
-                    const df gv = g.result();
-                    if (gv.hi < lmin) { lmin = gv.hi; fi = i; }
                 }
-                group_argmin(gmask, lmin, fi);
-                flip = fi;
-            }
-        } else {
-            flip = -2;
-        }
-        if (flip == -1 && xsum.hi > 0.f) {
-            // KKT holds: abundances and uncertainties
-            for (int i = t; i < P; i += XG)
-                if (!((m >> i) & 1ULL)) a.x_out[base + i] = 0.f;
+                group_argmin(gmask, xmin, fr);
+                xsum = group_sum_df(gmask, xsum);
+                if (fr >= 0) flip = (k == 1) ? -2 : sidx[fr];
+                if (flip == -1) {
+                    // most negative multiplier off S, coordinates spread over the lanes
 #pragma unroll
-            for (int s = 0; s < KS; ++s) {
-                const int r = s * XG + t;
-                if (r < k) a.x_out[base + sidx[r]] = xs[s].hi > 0.f ? df_div(xs[s], xsum).hi : 0.f;
+                    for (int s = 0; s < KS; ++s) {
+                        const int r = s * XG + t;
+                        if (r < k) { xh[r] = xs[s].hi; xl[r] = xs[s].lo; }
+                    }
+                    __syncwarp(gmask);
+                    float lmin = (float)-a.tol_g;
+                    int fi = -1;
+                    for (int i = t; i < P; i += XG) {
+                        if ((m >> i) & 1ULL) continue;
+                        dot2 g;
+                        for (int q = 0; q < k; ++q) {
+                            const float gh = sGh[i * P + sidx[q]], gl = sGl[i * P + sidx[q]];
+                            g.add_prod(gh, xh[q]);
+                            g.c = fmaf(gh, xl[q], fmaf(gl, xh[q], g.c));
+                        }
+                        g.add_df(df{-a.c_hi[base + i], -a.c_lo[base + i]});
+                        g.add_df(nu);
+                        const df gv = g.result();
+                        if (gv.hi < lmin) { lmin = gv.hi; fi = i; }
+                    }
+                    group_argmin(gmask, lmin, fi);
+                    flip = fi;
+                }
+            } else {
+                flip = -2;
             }
-            if (a.sx_out) {
-                // L -> L^-1 in place: Linv_ij = -(sum_{j<q<=i} Linv_iq L_qj) / L_jj,
-                // column j from right to left (rows on their lanes)
-                for (int j = k - 2; j >= 0; --j) {
-                    const df rlj = df{Lh[pk(j, j)], Ll[pk(j, j)]};
-                    df acc[KS];
+            if (flip == -1 && xsum.hi > 0.f) {
+                // KKT holds: abundances and uncertainties
+                for (int i = t; i < P; i += XG)
+                    if (!((m >> i) & 1ULL)) a.x_out[base + i] = 0.f;
 #pragma unroll
-                    for (int s = 0; s < KS; ++s) acc[s] = zero;
-                    for (int q = j + 1; q < k; ++q) {
-                        const df lqj = df{Lh[pk(q, j)], Ll[pk(q, j)]};
+                for (int s = 0; s < KS; ++s) {
+                    const int r = s * XG + t;
+                    if (r < k) a.x_out[base + sidx[r]] = xs[s].hi > 0.f ? df_div(xs[s], xsum).hi : 0.f;
+                }
+                if (a.sx_out) {
+                    // L -> L^-1 in place: Linv_ij = -(sum_{j<q<=i} Linv_iq L_qj) / L_jj,
+                    // column j from right to left (rows on their lanes)
+                    for (int j = k - 2; j >= 0; --j) {
+                        const df rlj = df{Lh[pk(j, j)], Ll[pk(j, j)]};
+                        df acc[KS];
+#pragma unroll
+                        for (int s = 0; s < KS; ++s) acc[s] = zero;
+                        for (int q = j + 1; q < k; ++q) {
+                            const df lqj = df{Lh[pk(q, j)], Ll[pk(q, j)]};
+#pragma unroll
+                            for (int s = 0; s < KS; ++s) {
+                                const int i = s * XG + t;
+                                if (i >= q && i < k)
+                                    acc[s] = df_fms(acc[s], df{Lh[pk(i, q)], Ll[pk(i, q)]}, lqj);
+                            }
+                        }
+                        __syncwarp(gmask);               // column j read by every row
 #pragma unroll
                         for (int s = 0; s < KS; ++s) {
                             const int i = s * XG + t;
-                            if (i >= q && i < k)
-                                acc[s] = df_fms(acc[s], df{Lh[pk(i, q)], Ll[pk(i, q)]}, lqj);
+                            if (i > j && i < k) {
+                                const df v = df_mul(acc[s], rlj);
+                                Lh[pk(i, j)] = v.hi;
+                                Ll[pk(i, j)] = v.lo;
+                            }
+                        }
+                        __syncwarp(gmask);
+                    }
+                    const float sc = (float)a.scale[0];
+                    const df inv_a11 = df_div(df_make(1.f), a11);
+                    for (int i = t; i < P; i += XG)
+                        if (!((m >> i) & 1ULL)) a.sx_out[base + i] = 0.f;
+                    df nrm[KS];
+#pragma unroll
+                    for (int s = 0; s < KS; ++s) nrm[s] = zero;
+                    for (int i = t; i < k; ++i) {
+#pragma unroll
+                        for (int s = 0; s < KS; ++s) {
+                            const int j = s * XG + t;
+                            if (j <= i) {
+                                const df w = df{Lh[pk(i, j)], Ll[pk(i, j)]};
+                                nrm[s] = df_add(nrm[s], df_mul(w, w));
+                            }
                         }
                     }
-                    __syncwarp(gmask);               // column j read by every row
-#pragma unroll
-                    for (int s = 0; s < KS; ++s) {
-                        const int i = s * XG + t;
-                        if (i > j && i < k) {
-                            const df v = df_mul(acc[s], rlj);
-                            Lh[pk(i, j)] = v.hi;
-                            Ll[pk(i, j)] = v.lo;
-                        }
-                    }
-                    __syncwarp(gmask);
-                }
-                const float sc = (float)a.scale[0];
-                const df inv_a11 = df_div(df_make(1.f), a11);
-                for (int i = t; i < P; i += XG)
-                    if (!((m >> i) & 1ULL)) a.sx_out[base + i] = 0.f;
-                df nrm[KS];
-#pragma unroll
-                for (int s = 0; s < KS; ++s) nrm[s] = zero;
-                for (int i = t; i < k; ++i) {
 #pragma unroll
                     for (int s = 0; s < KS; ++s) {
                         const int j = s * XG + t;
-                        if (j <= i) {
-                            const df w = df{Lh[pk(i, j)], Ll[pk(i, j)]};
-                            nrm[s] = df_add(nrm[s], df_mul(w, w));
+                        if (j < k) {
+                            const df var = df_sub(nrm[s], df_mul(df_mul(ub[s], ub[s]), inv_a11));
+                            a.sx_out[base + sidx[j]] = sqrtf(fmaxf(var.hi, 0.f) / sc);
                         }
                     }
                 }
-#pragma unroll
-                for (int s = 0; s < KS; ++s) {
-                    const int j = s * XG + t;
-                    if (j < k) {
-                        const df var = df_sub(nrm[s], df_mul(df_mul(ub[s], ub[s]), inv_a11));
-                        a.sx_out[base + sidx[j]] = sqrtf(fmaxf(var.hi, 0.f) / sc);
+                break;
+            } else if (flip >= 0 && can_flip) {
+                m ^= 1ULL << flip;
+                if (t == 0) a.mask[n] = m;
+                __syncwarp(gmask);                       // sidx, xh, xl are rewritten
+                continue;
+            } else {
+                // not finished here: retry list, or (retry path) keep the iterate
+                if (t == 0) {
+                    if (a.retry_list) {
+                        const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
+                        a.retry_list[pos] = n;
+                    } else if (a.n_unverified) {
+                        // the iterate stays as the result: reported as not converged
+                        if (!a.it_mark || a.it_mark[n] > 0) {
+                            atomicAdd(a.n_unverified, 1ULL);
+                            if (a.it_mark) a.it_mark[n] = -a.it_mark[n];
+                        }
                     }
                 }
-            }
-        } else if (flip >= 0 && a.list_out) {
-            if (t == 0) {
-                a.mask[n] = m ^ (1ULL << flip);
-                const unsigned long long pos = atomicAdd(a.len_out, 1ULL);
-                a.list_out[pos] = n;
-            }
-        } else {
-            // not finished here: retry list, or (retry path) keep the iterate
-            if (t == 0) {
-                if (a.retry_list) {
-                    const unsigned long long pos = atomicAdd(a.retry_len, 1ULL);
-                    a.retry_list[pos] = n;
-                } else if (a.n_unverified) {
-                    // the iterate stays as the result: reported as not converged
-                    if (!a.it_mark || a.it_mark[n] > 0) {
-                        atomicAdd(a.n_unverified, 1ULL);
-                        if (a.it_mark) a.it_mark[n] = -a.it_mark[n];
-                    }
+                for (int i = t; i < P; i += XG) {
+                    if (a.x_out != a.x_in) a.x_out[base + i] = a.x_in[base + i];
+                    if (a.sx_out) a.sx_out[base + i] = 0.f;
                 }
-            }
-            for (int i = t; i < P; i += XG) {
-                if (a.x_out != a.x_in) a.x_out[base + i] = a.x_in[base + i];
-                if (a.sx_out) a.sx_out[base + i] = 0.f;
+                break;
             }
         }
         __syncwarp(gmask);                           // the group's shared memory is reused
@@ -1076,21 +1083,30 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // pass p reads list (p & 1) (pass 0: the sorted list, or the given one)
-    // and writes list ((p + 1) & 1); the sorted list lives in w.list[0]
-    for (int pass = 0; pass <= MAX_SWAPS; ++pass) {
-        CrossArgs a = base;
-        a.list_in = pass == 0 ? first : w.list[pass & 1];
-        a.len_in = pass == 0 ? first_len : w.len + pass;
-        const bool last = pass == MAX_SWAPS;
-        a.list_out = last ? nullptr : w.list[(pass + 1) & 1];
-        a.len_out = last ? nullptr : w.len + pass + 1;
-        // pass 0 over the whole cube is throughput bound: thread per pixel;
-        // every other pass holds few pixels and is latency bound: lane groups
-        e = (pass == 0 && !list) ? launch_pass(a, st) : launch_pass_group(a, st);
+    // whole cube: pass 0 one thread per pixel (throughput bound), the
+    // pixels it flips go to list 1; then one launch of lane groups that
+    // takes each listed pixel through up to MAX_SWAPS further support
+    // changes (latency bound, few pixels).  A given list: the lane groups
+    // from its first solve, MAX_SWAPS + 1 solves.
+    CrossArgs a = base;
+    if (!list) {
+        a.list_in = first;
+        a.len_in = first_len;
+        a.list_out = w.list[1];
+        a.len_out = w.len + 1;
+        e = launch_pass(a, st);
         if (e != cudaSuccess) return e;
+        a.list_in = w.list[1];
+        a.len_in = w.len + 1;
+        a.max_solves = MAX_SWAPS;
+    } else {
+        a.list_in = first;
+        a.len_in = first_len;
+        a.max_solves = MAX_SWAPS + 1;
     }
-    return cudaSuccess;
+    a.list_out = nullptr;
+    a.len_out = nullptr;
+    return launch_pass_group(a, st);
 }
 
 // ------------------------------------------------------------------- rms

@@ -43,7 +43,7 @@ struct Prep {
 // them so that the launch count the C ABI reports stays exact)
 constexpr int PREP_LAUNCHES = 3;
 constexpr int PREP_COV_LAUNCHES = 4;
-constexpr int crossover_launches(bool whole_cube) { return (whole_cube ? 3 : 1) + MAX_SWAPS + 1; }
+constexpr int crossover_launches(bool whole_cube) { return whole_cube ? 3 + 2 : 1 + 1; }
 
 cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP,
                         const Prep &o, cudaStream_t st);
@@ -112,6 +112,7 @@ struct CrossArgs {
     unsigned long long *n_unverified;   // counted when retry_list is NULL
     int *it_mark;                  // with n_unverified: iteration counts, negated
                                    // (not converged) for a pixel left unverified
+    int max_solves;                // lane-group kernel: support solves per pixel
     double tol_x, tol_g;
 };
 
@@ -127,7 +128,9 @@ struct CrossoverScratch {
 };
 
 // Crossover of the pixels in list (or of all N pixels, sorted by support
-// size, when list is NULL): up to MAX_SWAPS + 1 passes.
+// size, when list is NULL): up to MAX_SWAPS + 1 support solves per pixel
+// (all N: a pass of one thread per pixel, then one lane-group launch for
+// the pixels it flipped; a list: one lane-group launch).
 cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
                              const long long *list, const unsigned long long *list_len,
                              cudaStream_t st);
