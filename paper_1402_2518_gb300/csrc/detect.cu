@@ -24,7 +24,7 @@ namespace {
 
 constexpr int DTH = 256;                 // threads per block
 constexpr int DBLOCKS = 152 * 4;         // blocks (8 warps each)
-constexpr int DU = 4;                    // pixels per warp step (loads in flight)
+constexpr int DU = 8;                    // pixels per warp step (loads in flight)
 constexpr unsigned FULLM = 0xffffffffu;
 
 struct DetectArgs {
@@ -58,23 +58,25 @@ __device__ __forceinline__ void warp_range(long long N, long long &n0, long long
 }
 
 struct MinAcc {
-    long long cnt = 0, ntr = 0, tp = 0, fp = 0;
+    int cnt = 0, ntr = 0, tp = 0, fp = 0;    // per warp range: < 2^31 pixels
     double xsum = 0.0;
     unsigned long long key = 0;
 };
 
+// TWO: minerals 32..63 exist (n_minerals > 32), the lane owns two.
+template <bool TWO>
 __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int P = a.P, nm = a.nm;
     const int i0 = lane, i1 = lane + 32;
-    const bool has0 = i0 < nm, has1 = i1 < nm;
+    const bool has0 = i0 < nm, has1 = TWO && i1 < nm;
     const float xm0 = has0 ? a.xmin[i0] : 0.f, xm1 = has1 ? a.xmin[i1] : 0.f;
     MinAcc m0, m1;
     long long n0, n1;
     warp_range(a.N, n0, n1);
     for (long long nb = n0; nb < n1; nb += DU) {
-        float xv0[DU], xv1[DU], sv0[DU], sv1[DU];
+        float xv0[DU], xv1[TWO ? DU : 1], sv0[DU], sv1[TWO ? DU : 1];
         bool ok[DU];
         unsigned long long tr[DU];
 #pragma unroll
@@ -83,11 +85,11 @@ __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
             const bool in = n < n1;
             const float *xr = a.x + n * P;
             xv0[u] = in && has0 ? __ldg(xr + i0) : 0.f;
-            xv1[u] = in && has1 ? __ldg(xr + i1) : 0.f;
+            if (TWO) xv1[u] = in && has1 ? __ldg(xr + i1) : 0.f;
             if (a.sx) {
                 const float *sr = a.sx + n * P;
                 sv0[u] = in && has0 ? __ldg(sr + i0) : 0.f;
-                sv1[u] = in && has1 ? __ldg(sr + i1) : 0.f;
+                if (TWO) sv1[u] = in && has1 ? __ldg(sr + i1) : 0.f;
             }
             bool o = in;
             if (in && a.rms) o = __ldg(a.rms + n) < a.rms_max;
@@ -99,12 +101,13 @@ __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
         for (int u = 0; u < DU; ++u) {
             const long long n = nb + u;
             bool d0 = ok[u] && has0 && xv0[u] > xm0;
-            bool d1 = ok[u] && has1 && xv1[u] > xm1;
+            bool d1 = TWO && ok[u] && has1 && xv1[TWO ? u : 0] > xm1;
             if (a.sx) {
                 d0 = d0 && sv0[u] < xv0[u];
-                d1 = d1 && sv1[u] < xv1[u];
+                if (TWO) d1 = d1 && sv1[TWO ? u : 0] < xv1[TWO ? u : 0];
             }
-            const unsigned b0 = __ballot_sync(FULLM, d0), b1 = __ballot_sync(FULLM, d1);
+            const unsigned b0 = __ballot_sync(FULLM, d0);
+            const unsigned b1 = TWO ? __ballot_sync(FULLM, d1) : 0u;
             if (n >= n1) continue;
             if (lane == 0 && a.mask) a.mask[n] = (unsigned long long)b0 | ((unsigned long long)b1 << 32);
             const bool t0 = (tr[u] >> i0) & 1ull, t1 = i1 < 64 && ((tr[u] >> i1) & 1ull);
@@ -116,11 +119,11 @@ __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
                     m0.key = k > m0.key ? k : m0.key;
                 }
             }
-            if (has1) {
+            if (TWO && has1) {
                 m1.ntr += t1; m1.tp += d1 && t1; m1.fp += d1 && !t1;
                 if (d1) {
-                    ++m1.cnt; m1.xsum += (double)xv1[u];
-                    const unsigned long long k = max_key(xv1[u], n);
+                    ++m1.cnt; m1.xsum += (double)xv1[TWO ? u : 0];
+                    const unsigned long long k = max_key(xv1[TWO ? u : 0], n);
                     m1.key = k > m1.key ? k : m1.key;
                 }
             }
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
     }
     if (!a.out) return;
     linmin_detection *o = a.out;
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < (TWO ? 2 : 1); ++h) {
         const int i = h ? i1 : i0;
         const MinAcc &m = h ? m1 : m0;
         if (i >= nm) continue;
@@ -295,7 +298,10 @@ linmin_status linmin_detect(const float *x, const float *sx, const float *rms,
         a.N = N; a.P = P; a.nm = n_minerals; a.rms_max = rms_max; a.mask = mask;
         a.out = out;
         for (int i = 0; i < LINMIN_MAX_P; ++i) a.xmin[i] = i < n_minerals ? x_min[i] : 0.f;
-        detect_kernel<<<grid_for(N), DTH, 0, s>>>(a);
+        if (n_minerals > 32)
+            detect_kernel<true><<<grid_for(N), DTH, 0, s>>>(a);
+        else
+            detect_kernel<false><<<grid_for(N), DTH, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "linmin_detect: launch");
     }
     if (out) {
