@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-constraints", action="store_true", help="skip the slo / pos leg")
     ap.add_argument("--no-detection", action="store_true", help="skip the detection leg")
     ap.add_argument("--no-second-pass", action="store_true", help="skip the second-pass timing")
+    ap.add_argument("--detect-flush-gb", type=float, default=4.0,
+                    help="GiB written before each timed detection call")
     ap.add_argument("--precision", default="tc", choices=["df", "tc", "bf16"],
                     help="projection: double-float CUDA cores, exact tensor-core slices, bf16")
     ap.add_argument("--serving-cubes", type=int, default=64)
@@ -375,7 +377,7 @@ def run_constraints(pkg, dev, n_pix: int, steps: int):
 
 
 def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
-                  n_second: bool = True):
+                  n_second: bool = True, flush_gb: float = 4.0):
     """Detection products on the unmixed cube: eq. Threshold from the known
     truth (threshold sums kernel), then the per-pixel detection kernel with
     the three conditions of Sec. 5.  Each detection launch is timed alone
@@ -394,7 +396,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
     # 4 GiB: flushes L2 and keeps the device busy (~0.7 ms) while the host
     # queues the timed call (pointer checks, memset, two launches), so that
     # the events bracket the kernels alone
-    flush = torch.empty((4 << 30,), dtype=torch.uint8, device=dev)
+    flush = torch.empty((int(flush_gb * (1 << 30)),), dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
     pkg.linmin_threshold_stats(x, truth, N, P, nm, sums, stream=stream)
     torch.cuda.synchronize()
@@ -467,7 +469,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
             "roofline": {"kernel": "detect_kernel", "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                          "bytes_per_pixel": 8 * P + 24, "traffic": None,
-                         "l2": "4 GiB write before each timed launch"},
+                         "l2": f"{flush_gb:g} GiB write before each timed launch"},
             "thresholds": "eq. Threshold from the truth of the cube (population std)",
             "rms_max": rms_max,
             "positive_detection": int(d["true_pos"][:nm].sum()) / max(nt, 1),
@@ -567,7 +569,7 @@ def main():
     if not args.no_detection and rank == 0:
         detection = run_detection(pkg, dev, cube, x, sx, rms, it, max(3, args.steps // 2),
                                   float(measured_peaks().get("hbm_gbs", 6800.0)),
-                                  not args.no_second_pass)
+                                  not args.no_second_pass, args.detect_flush_gb)
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,
