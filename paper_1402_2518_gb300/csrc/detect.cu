@@ -7,7 +7,8 @@
 // lane i reads x[n, i] (and x[n, i + 32]; a pixel's row is one coalesced
 // read), decides mineral i, and a warp ballot gives the pixel's detection
 // mask; each lane keeps its mineral's counts, sum and arg-max in registers
-// over the whole range, with one atomic per mineral and warp at the end.
+// over the whole range; the block sums its warps in shared memory and
+// issues one atomic per mineral and block.
 // Memory bound: 4P (x) + 4P (sx) + 16 bytes read and 8 bytes written per
 // pixel.
 #include <cuda_runtime.h>
@@ -130,21 +131,45 @@ __global__ void __launch_bounds__(DTH) detect_kernel(DetectArgs a)
         }
     }
     if (!a.out) return;
-    linmin_detection *o = a.out;
-    for (int h = 0; h < (TWO ? 2 : 1); ++h) {
-        const int i = h ? i1 : i0;
+    // block reduction of the warps' sums (one atomic per mineral and block:
+    // same-address atomics from every warp serialise in L2)
+    __shared__ int s_cnt[DTH / 32][LINMIN_MAX_P], s_ntr[DTH / 32][LINMIN_MAX_P];
+    __shared__ int s_tp[DTH / 32][LINMIN_MAX_P], s_fp[DTH / 32][LINMIN_MAX_P];
+    __shared__ double s_sum[DTH / 32][LINMIN_MAX_P];
+    __shared__ unsigned long long s_key[DTH / 32][LINMIN_MAX_P];
+    const int w = threadIdx.x >> 5;
+    for (int h = 0; h < 2; ++h) {
         const MinAcc &m = h ? m1 : m0;
-        if (i >= nm) continue;
-        if (m.cnt) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&o->count[i]), (unsigned long long)m.cnt);
-            atomicAdd(&o->xsum[i], m.xsum);
-            atomicMax(&o->key[i], m.key);
-        }
-        if (a.truth) {
-            if (m.ntr) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_true[i]), (unsigned long long)m.ntr);
-            if (m.tp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->true_pos[i]), (unsigned long long)m.tp);
-            if (m.fp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->false_pos[i]), (unsigned long long)m.fp);
-        }
+        const int i = lane + 32 * h;
+        const bool own = h == 0 || TWO;
+        s_cnt[w][i] = own ? m.cnt : 0;
+        s_ntr[w][i] = own ? m.ntr : 0;
+        s_tp[w][i] = own ? m.tp : 0;
+        s_fp[w][i] = own ? m.fp : 0;
+        s_sum[w][i] = own ? m.xsum : 0.0;
+        s_key[w][i] = own ? m.key : 0ull;
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i >= nm) return;
+    long long cnt = 0, ntr = 0, tp = 0, fp = 0;
+    double xsum = 0.0;
+    unsigned long long key = 0;
+    for (int q = 0; q < DTH / 32; ++q) {
+        cnt += s_cnt[q][i]; ntr += s_ntr[q][i]; tp += s_tp[q][i]; fp += s_fp[q][i];
+        xsum += s_sum[q][i];
+        key = s_key[q][i] > key ? s_key[q][i] : key;
+    }
+    linmin_detection *o = a.out;
+    if (cnt) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&o->count[i]), (unsigned long long)cnt);
+        atomicAdd(&o->xsum[i], xsum);
+        atomicMax(&o->key[i], key);
+    }
+    if (a.truth) {
+        if (ntr) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_true[i]), (unsigned long long)ntr);
+        if (tp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->true_pos[i]), (unsigned long long)tp);
+        if (fp) atomicAdd(reinterpret_cast<unsigned long long *>(&o->false_pos[i]), (unsigned long long)fp);
     }
 }
 
@@ -190,14 +215,34 @@ __global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
             else                 { ++nn[h]; sn[h] += v; qn[h] += v * v; }
         }
     }
-    linmin_threshold_sums *o = a.out;
+    __shared__ long long s_np[DTH / 32][LINMIN_MAX_P], s_nn[DTH / 32][LINMIN_MAX_P];
+    __shared__ double s_sp[DTH / 32][LINMIN_MAX_P], s_qp[DTH / 32][LINMIN_MAX_P];
+    __shared__ double s_sn[DTH / 32][LINMIN_MAX_P], s_qn[DTH / 32][LINMIN_MAX_P];
+    const int w = threadIdx.x >> 5;
     for (int h = 0; h < 2; ++h) {
         const int i = lane + 32 * h;
-        if (i >= nm) continue;
-        if (np[h]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)np[h]);
-        if (nn[h]) atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)nn[h]);
-        if (np[h]) { atomicAdd(&o->sum_pos[i], sp[h]); atomicAdd(&o->sumsq_pos[i], qp[h]); }
-        if (nn[h]) { atomicAdd(&o->sum_neg[i], sn[h]); atomicAdd(&o->sumsq_neg[i], qn[h]); }
+        s_np[w][i] = np[h]; s_nn[w][i] = nn[h];
+        s_sp[w][i] = sp[h]; s_qp[w][i] = qp[h]; s_sn[w][i] = sn[h]; s_qn[w][i] = qn[h];
+    }
+    __syncthreads();
+    const int i = threadIdx.x;
+    if (i >= nm) return;
+    long long tnp = 0, tnn = 0;
+    double tsp = 0.0, tqp = 0.0, tsn = 0.0, tqn = 0.0;
+    for (int q = 0; q < DTH / 32; ++q) {
+        tnp += s_np[q][i]; tnn += s_nn[q][i];
+        tsp += s_sp[q][i]; tqp += s_qp[q][i]; tsn += s_sn[q][i]; tqn += s_qn[q][i];
+    }
+    linmin_threshold_sums *o = a.out;
+    if (tnp) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)tnp);
+        atomicAdd(&o->sum_pos[i], tsp);
+        atomicAdd(&o->sumsq_pos[i], tqp);
+    }
+    if (tnn) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)tnn);
+        atomicAdd(&o->sum_neg[i], tsn);
+        atomicAdd(&o->sumsq_neg[i], tqn);
     }
 }
 

@@ -224,25 +224,38 @@ __global__ void strip_slack_kernel(const float *__restrict__ xa, const float *__
     }
 }
 
+// A warp walks a contiguous range of pixels, lane j holds columns j and
+// j + 32 of the pixel's c~ row (coalesced row reads and writes).
 __global__ void exclude_kernel(const unsigned long long *__restrict__ mask, int n_minerals,
                                float *c_hi, float *c_lo, long long N, int P)
 {
     const unsigned long long keep =
         n_minerals >= 64 ? ~0ull : ((1ull << n_minerals) - 1ull);
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
-         n += (long long)gridDim.x * blockDim.x) {
-        const unsigned long long drop = keep & ~mask[n];
-        if (!drop) continue;
-        float* hi = c_hi + n * P;
-        float* lo = c_lo + n * P;
-        float cmax = 0.f;
-        for (int j = 0; j < P; ++j) cmax = fmaxf(cmax, fabsf(hi[j] + lo[j]));
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long per = (N + nw - 1) / nw;
+    const long long n0 = w * per, n1 = n0 + per < N ? n0 + per : N;
+    for (long long n = n0; n < n1; ++n) {
+        const unsigned long long drop = keep & ~__ldg(mask + n);
+        if (!drop) continue;                            // warp-uniform
+        float *hi = c_hi + n * P;
+        float *lo = c_lo + n * P;
+        const int j0 = lane, j1 = lane + 32;
+        const float h0 = j0 < P ? hi[j0] : 0.f, l0 = j0 < P ? lo[j0] : 0.f;
+        const float h1 = j1 < P ? hi[j1] : 0.f, l1 = j1 < P ? lo[j1] : 0.f;
+        float cmax = fmaxf(fabsf(h0 + l0), fabsf(h1 + l1));
+        for (int off = 16; off; off >>= 1) cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, off));
         const float K = 2.f * (cmax + (float)P + (float)RHO) + 1.f;
-        for (int j = 0; j < n_minerals; ++j) {
-            if (!((drop >> j) & 1ull)) continue;
-            const df r = df_add(df{hi[j], lo[j]}, df_make(-K));
-            hi[j] = r.hi;
-            lo[j] = r.lo;
+        if ((drop >> j0) & 1ull) {
+            const df r = df_add(df{h0, l0}, df_make(-K));
+            hi[j0] = r.hi;
+            lo[j0] = r.lo;
+        }
+        if (j1 < 64 && ((drop >> j1) & 1ull)) {
+            const df r = df_add(df{h1, l1}, df_make(-K));
+            hi[j1] = r.hi;
+            lo[j1] = r.lo;
         }
     }
 }
@@ -251,8 +264,10 @@ cudaError_t launch_exclude(const unsigned long long *mask, int n_minerals, float
                            float *c_lo, long long N, int P, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
-    const long long b = (N + 255) / 256;
-    exclude_kernel<<<(int)(b < 4096 ? b : 4096), 256, 0, st>>>(mask, n_minerals, c_hi, c_lo, N, P);
+    const long long warps = (N + 7) / 8;                // at least 8 pixels per warp
+    const long long b = (warps + 7) / 8;
+    exclude_kernel<<<(int)(b < 152 * 8 ? b : 152 * 8), 256, 0, st>>>(mask, n_minerals, c_hi, c_lo,
+                                                                     N, P);
     return cudaGetLastError();
 }
 
