@@ -78,6 +78,10 @@ struct linmin_ctx {
     __nv_bfloat16 *bsl = nullptr;
     int *fexp = nullptr;
     cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
+    // host-buffer pipeline: copy stream, per-chunk events, pinned counters
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t pev_in[4] = {}, pev_out[4] = {};
+    unsigned long long *pinned_cnt = nullptr;
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -425,7 +429,102 @@ static linmin_status load_cov(linmin_ctx *h, const double *cov_inv)
 static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
                                 const double *cov_inv, float *abundances, float *uncertainties,
                                 float *residual_rms, int *iterations,
-                                const unsigned long long *col_mask = nullptr, int n_minerals = 0)
+                                const unsigned long long *col_mask = nullptr, int n_minerals = 0);
+
+// Host buffers: the cube goes to the device in PIPE_CHUNKS pieces on a copy
+// stream, each piece is unmixed on the handle's stream as soon as it has
+// arrived, and its outputs go back on the copy stream while the next piece
+// is computed.  Synchronous, like every call with host buffers.
+constexpr int PIPE_CHUNKS = 4;
+constexpr long long PIPE_MIN_N = 65536;
+
+static linmin_status unmix_pipelined(linmin_ctx *h, const float *cube, long long N,
+                                     const float *sigma, const double *cov_inv,
+                                     float *abundances, float *uncertainties,
+                                     float *residual_rms, int *iterations,
+                                     const unsigned long long *col_mask, int n_minerals,
+                                     bool dev_cube, bool dev_sigma, const bool dev_out[4])
+{
+    const int L = h->L, UP = h->user_P;
+    cudaStream_t st = h->stream;
+    linmin_status s;
+    if ((s = ensure_io(h, N)) != LINMIN_OK) return s;
+    if (!h->cstream) {
+        LM_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking), "copy stream");
+        for (int k = 0; k < PIPE_CHUNKS; ++k) {
+            LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_in[k], cudaEventDisableTiming), "event");
+            LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_out[k], cudaEventDisableTiming), "event");
+        }
+        LM_CUDA(h, cudaMallocHost((void **)&h->pinned_cnt, PIPE_CHUNKS * sizeof(unsigned long long)),
+                "pinned counters");
+    }
+    cudaStream_t cs = h->cstream;
+    const float *d_sigma = sigma;
+    if (sigma && !dev_sigma) {
+        LM_CUDA(h, cudaMemcpyAsync(h->io_sigma, sigma, (size_t)L * 4, cudaMemcpyHostToDevice, st),
+                "copy sigma");
+        d_sigma = h->io_sigma;
+    }
+    const long long C = (N + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
+    // every input piece queued at once on the copy stream
+    if (!dev_cube) {
+        // the copy stream must not overwrite staging a previous call still reads
+        LM_CUDA(h, cudaEventRecord(h->pev_out[0], st), "event");
+        LM_CUDA(h, cudaStreamWaitEvent(cs, h->pev_out[0], 0), "event wait");
+        for (int k = 0; k < PIPE_CHUNKS; ++k) {
+            const long long off = k * C, nk = off < N ? (N - off < C ? N - off : C) : 0;
+            if (nk > 0)
+                LM_CUDA(h, cudaMemcpyAsync(h->io_cube + off * L, cube + off * L, (size_t)nk * L * 4,
+                                           cudaMemcpyHostToDevice, cs), "copy cube");
+            LM_CUDA(h, cudaEventRecord(h->pev_in[k], cs), "event");
+        }
+    }
+    int launches = 0;
+    for (int k = 0; k < PIPE_CHUNKS; ++k) {
+        h->pinned_cnt[k] = 0;
+        const long long off = k * C, nk = off < N ? (N - off < C ? N - off : C) : 0;
+        if (nk <= 0) continue;
+        if (!dev_cube) LM_CUDA(h, cudaStreamWaitEvent(st, h->pev_in[k], 0), "event wait");
+        const float *cin = (dev_cube ? cube : h->io_cube) + off * L;
+        float *xo = abundances ? (dev_out[0] ? abundances : h->io_x) + off * UP : nullptr;
+        float *so = uncertainties ? (dev_out[1] ? uncertainties : h->io_sx) + off * UP : nullptr;
+        float *ro = residual_rms ? (dev_out[2] ? residual_rms : h->io_rms) + off : nullptr;
+        int *io = iterations ? (dev_out[3] ? iterations : h->io_it) + off : nullptr;
+        s = unmix_impl(h, cin, nk, d_sigma, cov_inv, xo, so, ro, io,
+                       col_mask ? col_mask + off : nullptr, n_minerals);
+        if (s != LINMIN_OK) return s;
+        launches += h->launches;
+        LM_CUDA(h, cudaMemcpyAsync(h->pinned_cnt + k, h->dcnt + 2, sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, st), "read counter");
+        LM_CUDA(h, cudaEventRecord(h->pev_out[k], st), "event");
+        LM_CUDA(h, cudaStreamWaitEvent(cs, h->pev_out[k], 0), "event wait");
+        if (abundances && !dev_out[0])
+            LM_CUDA(h, cudaMemcpyAsync(abundances + off * UP, xo, (size_t)nk * UP * 4,
+                                       cudaMemcpyDeviceToHost, cs), "copy x");
+        if (uncertainties && !dev_out[1])
+            LM_CUDA(h, cudaMemcpyAsync(uncertainties + off * UP, so, (size_t)nk * UP * 4,
+                                       cudaMemcpyDeviceToHost, cs), "copy sx");
+        if (residual_rms && !dev_out[2])
+            LM_CUDA(h, cudaMemcpyAsync(residual_rms + off, ro, (size_t)nk * 4,
+                                       cudaMemcpyDeviceToHost, cs), "copy rms");
+        if (iterations && !dev_out[3])
+            LM_CUDA(h, cudaMemcpyAsync(iterations + off, io, (size_t)nk * 4,
+                                       cudaMemcpyDeviceToHost, cs), "copy iterations");
+    }
+    h->launches = launches;
+    LM_CUDA(h, cudaStreamSynchronize(cs), "output copies");
+    LM_CUDA(h, cudaStreamSynchronize(st), "kernel execution");
+    // the whole call's count where linmin_wait reads it
+    unsigned long long nbad = 0;
+    for (int k = 0; k < PIPE_CHUNKS; ++k) nbad += h->pinned_cnt[k];
+    LM_CUDA(h, cudaMemcpy(h->dcnt + 2, &nbad, sizeof(nbad), cudaMemcpyHostToDevice), "write counter");
+    return linmin_wait(h, nullptr);
+}
+
+static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
+                                const double *cov_inv, float *abundances, float *uncertainties,
+                                float *residual_rms, int *iterations,
+                                const unsigned long long *col_mask, int n_minerals)
 {
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
     if (N < 0) return fail(h, LINMIN_ERR_INVALID, "N < 0");
@@ -450,6 +549,9 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
             if (!(sigma[l] > 0.f) || !std::isfinite(sigma[l]))
                 return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
     }
+    if (host_any && N >= PIPE_MIN_N)
+        return unmix_pipelined(h, cube, N, sigma, cov_inv, abundances, uncertainties, residual_rms,
+                               iterations, col_mask, n_minerals, dev_cube, dev_sigma, dev_out);
     linmin_status s;
     if (cov_inv && (s = load_cov(h, cov_inv)) != LINMIN_OK) return s;
     if ((s = ensure_scratch(h, N)) != LINMIN_OK) return s;
@@ -828,6 +930,15 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->fexp, h->xa, h->sxa};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, h->stream);
+    if (h->cstream) {
+        cudaStreamSynchronize(h->cstream);
+        cudaStreamDestroy(h->cstream);
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (h->pev_in[k]) cudaEventDestroy(h->pev_in[k]);
+        if (h->pev_out[k]) cudaEventDestroy(h->pev_out[k]);
+    }
+    if (h->pinned_cnt) cudaFreeHost(h->pinned_cnt);
     if (h->pool) pool_release(h->device);
     delete h;
     return LINMIN_OK;

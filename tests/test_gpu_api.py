@@ -77,3 +77,27 @@ def test_autotune_and_lanes():
     assert e.value.status == linmin.LINMIN_ERR_UNSUPPORTED
     assert pkg.linmin_get_lanes(um.h) == 8                    # unchanged by the refusal
     um.close()
+
+
+def test_host_buffers_pipelined_equal_device():
+    """Host buffers of at least 65,536 pixels go through the copy/compute
+    pipeline (four pieces, copies on their own stream): the results equal
+    the device-pointer call bit for bit, with a ragged last piece and a
+    missing output."""
+    import paper_1402_2518_gb300 as pkg
+    pkg.load()
+    cube = synth.make_cube(synth.OMEGA_262K, n_pix=70001)
+    dev = torch.device("cuda:0")
+    um = pkg.Unmixer(torch.from_numpy(cube.S).to(dev))
+    X = torch.from_numpy(cube.X).to(dev)
+    sg = torch.from_numpy(cube.sigma).to(dev)
+    x, sx, rms, it = um(X, sg)
+    st, _ = um.wait()
+    assert st == 0
+    N, P = cube.N, cube.P
+    xh = np.empty((N, P), np.float32); rh = np.empty(N, np.float32); ih = np.empty(N, np.int32)
+    assert pkg.linmin_unmix(um.h, cube.X, N, cube.sigma, xh, None, rh, ih) == 0
+    np.testing.assert_array_equal(xh, x.cpu().numpy())
+    np.testing.assert_array_equal(rh, rms.cpu().numpy())
+    np.testing.assert_array_equal(ih, it.cpu().numpy())
+    um.close()
