@@ -78,10 +78,9 @@ struct linmin_ctx {
     __nv_bfloat16 *bsl = nullptr;
     int *fexp = nullptr;
     cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
-    // host-buffer pipeline: copy stream, per-chunk events, pinned counters
+    // host-buffer pipeline: copy stream and its events
     cudaStream_t cstream = nullptr;
     cudaEvent_t pev_in[4] = {}, pev_out[4] = {};
-    unsigned long long *pinned_cnt = nullptr;
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -431,94 +430,22 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
                                 float *residual_rms, int *iterations,
                                 const unsigned long long *col_mask = nullptr, int n_minerals = 0);
 
-// Host buffers: the cube goes to the device in PIPE_CHUNKS pieces on a copy
-// stream, each piece is unmixed on the handle's stream as soon as it has
-// arrived, and its outputs go back on the copy stream while the next piece
-// is computed.  Synchronous, like every call with host buffers.
+// Host cube of PIPE_MIN_N pixels or more: copied in PIPE_CHUNKS pieces on a
+// copy stream, the projection of each piece starts as soon as it has
+// arrived (the copy of the next piece overlaps it); with host outputs, x
+// and sigma_x go back on the copy stream while the RMS runs.
 constexpr int PIPE_CHUNKS = 4;
 constexpr long long PIPE_MIN_N = 65536;
 
-static linmin_status unmix_pipelined(linmin_ctx *h, const float *cube, long long N,
-                                     const float *sigma, const double *cov_inv,
-                                     float *abundances, float *uncertainties,
-                                     float *residual_rms, int *iterations,
-                                     const unsigned long long *col_mask, int n_minerals,
-                                     bool dev_cube, bool dev_sigma, const bool dev_out[4])
+static linmin_status ensure_copy_stream(linmin_ctx *h)
 {
-    const int L = h->L, UP = h->user_P;
-    cudaStream_t st = h->stream;
-    linmin_status s;
-    if ((s = ensure_io(h, N)) != LINMIN_OK) return s;
-    if (!h->cstream) {
-        LM_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking), "copy stream");
-        for (int k = 0; k < PIPE_CHUNKS; ++k) {
-            LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_in[k], cudaEventDisableTiming), "event");
-            LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_out[k], cudaEventDisableTiming), "event");
-        }
-        LM_CUDA(h, cudaMallocHost((void **)&h->pinned_cnt, PIPE_CHUNKS * sizeof(unsigned long long)),
-                "pinned counters");
-    }
-    cudaStream_t cs = h->cstream;
-    const float *d_sigma = sigma;
-    if (sigma && !dev_sigma) {
-        LM_CUDA(h, cudaMemcpyAsync(h->io_sigma, sigma, (size_t)L * 4, cudaMemcpyHostToDevice, st),
-                "copy sigma");
-        d_sigma = h->io_sigma;
-    }
-    const long long C = (N + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
-    // every input piece queued at once on the copy stream
-    if (!dev_cube) {
-        // the copy stream must not overwrite staging a previous call still reads
-        LM_CUDA(h, cudaEventRecord(h->pev_out[0], st), "event");
-        LM_CUDA(h, cudaStreamWaitEvent(cs, h->pev_out[0], 0), "event wait");
-        for (int k = 0; k < PIPE_CHUNKS; ++k) {
-            const long long off = k * C, nk = off < N ? (N - off < C ? N - off : C) : 0;
-            if (nk > 0)
-                LM_CUDA(h, cudaMemcpyAsync(h->io_cube + off * L, cube + off * L, (size_t)nk * L * 4,
-                                           cudaMemcpyHostToDevice, cs), "copy cube");
-            LM_CUDA(h, cudaEventRecord(h->pev_in[k], cs), "event");
-        }
-    }
-    int launches = 0;
-    for (int k = 0; k < PIPE_CHUNKS; ++k) {
-        h->pinned_cnt[k] = 0;
-        const long long off = k * C, nk = off < N ? (N - off < C ? N - off : C) : 0;
-        if (nk <= 0) continue;
-        if (!dev_cube) LM_CUDA(h, cudaStreamWaitEvent(st, h->pev_in[k], 0), "event wait");
-        const float *cin = (dev_cube ? cube : h->io_cube) + off * L;
-        float *xo = abundances ? (dev_out[0] ? abundances : h->io_x) + off * UP : nullptr;
-        float *so = uncertainties ? (dev_out[1] ? uncertainties : h->io_sx) + off * UP : nullptr;
-        float *ro = residual_rms ? (dev_out[2] ? residual_rms : h->io_rms) + off : nullptr;
-        int *io = iterations ? (dev_out[3] ? iterations : h->io_it) + off : nullptr;
-        s = unmix_impl(h, cin, nk, d_sigma, cov_inv, xo, so, ro, io,
-                       col_mask ? col_mask + off : nullptr, n_minerals);
-        if (s != LINMIN_OK) return s;
-        launches += h->launches;
-        LM_CUDA(h, cudaMemcpyAsync(h->pinned_cnt + k, h->dcnt + 2, sizeof(unsigned long long),
-                                   cudaMemcpyDeviceToHost, st), "read counter");
-        LM_CUDA(h, cudaEventRecord(h->pev_out[k], st), "event");
-        LM_CUDA(h, cudaStreamWaitEvent(cs, h->pev_out[k], 0), "event wait");
-        if (abundances && !dev_out[0])
-            LM_CUDA(h, cudaMemcpyAsync(abundances + off * UP, xo, (size_t)nk * UP * 4,
-                                       cudaMemcpyDeviceToHost, cs), "copy x");
-        if (uncertainties && !dev_out[1])
-            LM_CUDA(h, cudaMemcpyAsync(uncertainties + off * UP, so, (size_t)nk * UP * 4,
-                                       cudaMemcpyDeviceToHost, cs), "copy sx");
-        if (residual_rms && !dev_out[2])
-            LM_CUDA(h, cudaMemcpyAsync(residual_rms + off, ro, (size_t)nk * 4,
-                                       cudaMemcpyDeviceToHost, cs), "copy rms");
-        if (iterations && !dev_out[3])
-            LM_CUDA(h, cudaMemcpyAsync(iterations + off, io, (size_t)nk * 4,
-                                       cudaMemcpyDeviceToHost, cs), "copy iterations");
-    }
-    h->launches = launches;
-    LM_CUDA(h, cudaStreamSynchronize(cs), "output copies");
-    LM_CUDA(h, cudaStreamSynchronize(st), "kernel execution");
-    // the whole call's count where linmin_wait reads it
-    unsigned long long nbad = 0;
-    for (int k = 0; k < PIPE_CHUNKS; ++k) nbad += h->pinned_cnt[k];
-    LM_CUDA(h, cudaMemcpy(h->dcnt + 2, &nbad, sizeof(nbad), cudaMemcpyHostToDevice), "write counter");
-    return linmin_wait(h, nullptr);
+    if (h->cstream) return LINMIN_OK;
+    LM_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking), "copy stream");
+    for (int k = 0; k < PIPE_CHUNKS; ++k)
+        LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_in[k], cudaEventDisableTiming), "event");
+    LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_out[0], cudaEventDisableTiming), "event");
+    LM_CUDA(h, cudaEventCreateWithFlags(&h->pev_out[1], cudaEventDisableTiming), "event");
+    return LINMIN_OK;
 }
 
 static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
@@ -549,9 +476,6 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
             if (!(sigma[l] > 0.f) || !std::isfinite(sigma[l]))
                 return fail(h, LINMIN_ERR_INVALID, "sigma must be finite and > 0");
     }
-    if (host_any && N >= PIPE_MIN_N)
-        return unmix_pipelined(h, cube, N, sigma, cov_inv, abundances, uncertainties, residual_rms,
-                               iterations, col_mask, n_minerals, dev_cube, dev_sigma, dev_out);
     linmin_status s;
     if (cov_inv && (s = load_cov(h, cov_inv)) != LINMIN_OK) return s;
     if ((s = ensure_scratch(h, N)) != LINMIN_OK) return s;
@@ -559,7 +483,28 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
 
     const size_t np = (size_t)N * h->user_P;    // caller-visible N x P outputs
     const float *d_cube = cube, *d_sigma = sigma;
-    if (!dev_cube) {
+    const bool piped = !dev_cube && N >= PIPE_MIN_N;
+    const long long PC = (N + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
+    auto piece = [&](int k, long long &off, long long &nk) {
+        off = k * PC;
+        nk = off < N ? (N - off < PC ? N - off : PC) : 0;
+    };
+    if (piped) {
+        if ((s = ensure_copy_stream(h)) != LINMIN_OK) return s;
+        // after the work already queued on the handle's stream (it may read
+        // the staging buffer), the pieces of the cube on the copy stream
+        LM_CUDA(h, cudaEventRecord(h->pev_out[0], st), "event");
+        LM_CUDA(h, cudaStreamWaitEvent(h->cstream, h->pev_out[0], 0), "event wait");
+        for (int k = 0; k < PIPE_CHUNKS; ++k) {
+            long long off, nk;
+            piece(k, off, nk);
+            if (nk > 0)
+                LM_CUDA(h, cudaMemcpyAsync(h->io_cube + off * L, cube + off * L, (size_t)nk * L * 4,
+                                           cudaMemcpyHostToDevice, h->cstream), "copy cube");
+            LM_CUDA(h, cudaEventRecord(h->pev_in[k], h->cstream), "event");
+        }
+        d_cube = h->io_cube;
+    } else if (!dev_cube) {
         LM_CUDA(h, cudaMemcpyAsync(h->io_cube, cube, (size_t)N * L * 4, cudaMemcpyHostToDevice, st),
                 "copy cube");
         d_cube = h->io_cube;
@@ -589,11 +534,8 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     else
         LM_CUDA(h, launch_prep(h->dS, d_sigma, L, P, h->bucket.PP, h->prep, st), "prep kernels");
     mark(h, 1);
-    int proj_launches = 1;
-    if (h->opt.precision == LINMIN_PROJ_DF) {
-        LM_CUDA(h, launch_project(d_cube, N, L, P, h->prep.Bhi, h->prep.Blo, h->c_hi, h->c_lo, st),
-                "projection kernel");
-    } else {
+    int proj_launches = 0;
+    if (h->opt.precision != LINMIN_PROJ_DF) {
         if (!cov_inv) {
             LM_CUDA(h, launch_prep_t_diag(h->dS, d_sigma, L, P, h->covT, st), "projection prep");
             ++proj_launches;
@@ -601,14 +543,29 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
         LM_CUDA(h, launch_tc_prep(h->covT, L, P, h->prep.scale, h->opt.precision, h->bsl, h->fexp,
                                   st), "projection prep");
         proj_launches += h->opt.precision == LINMIN_PROJ_TC ? 2 : 1;
-        if (h->opt.precision == LINMIN_PROJ_TC && tc2_usable(d_cube, N, L)) {
-            LM_CUDA(h, launch_project_tc2(d_cube, N, L, P, h->bsl, h->fexp, h->rexp, h->c_hi,
-                                          h->c_lo, h->prep.flags, st), "tensor-core projection");
+    }
+    // the projection, piece by piece as the cube arrives when piped
+    for (int k = 0; k < (piped ? PIPE_CHUNKS : 1); ++k) {
+        long long off = 0, nk = N;
+        if (piped) {
+            piece(k, off, nk);
+            LM_CUDA(h, cudaStreamWaitEvent(st, h->pev_in[k], 0), "event wait");
+            if (nk <= 0) continue;
+        }
+        const float *cin = d_cube + off * L;
+        float *chi = h->c_hi + off * P, *clo = h->c_lo + off * P;
+        if (h->opt.precision == LINMIN_PROJ_DF) {
+            LM_CUDA(h, launch_project(cin, nk, L, P, h->prep.Bhi, h->prep.Blo, chi, clo, st),
+                    "projection kernel");
             ++proj_launches;
+        } else if (h->opt.precision == LINMIN_PROJ_TC && tc2_usable(cin, nk, L)) {
+            LM_CUDA(h, launch_project_tc2(cin, nk, L, P, h->bsl, h->fexp, h->rexp + off, chi, clo,
+                                          h->prep.flags, st), "tensor-core projection");
+            proj_launches += 2;
         } else {
-            LM_CUDA(h, launch_project_tc(d_cube, N, L, P, h->opt.precision, h->bsl, h->fexp,
-                                         h->c_hi, h->c_lo, h->prep.flags, st),
-                    "tensor-core projection");
+            LM_CUDA(h, launch_project_tc(cin, nk, L, P, h->opt.precision, h->bsl, h->fexp, chi, clo,
+                                         h->prep.flags, st), "tensor-core projection");
+            ++proj_launches;
         }
     }
     if (col_mask) {
@@ -646,6 +603,19 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     ca.it_mark = h->it;
     LM_CUDA(h, launch_crossover(ca, h->xw, h->retry, h->dcnt + 5, st), "retry crossover kernels");
     mark(h, 5);
+    // host x and sigma_x: final here without a slack; copied back on the
+    // copy stream while the RMS runs
+    const bool early_out = piped && !h->slack;
+    if (early_out && ((abundances && !dev_out[0]) || (uncertainties && !dev_out[1]))) {
+        LM_CUDA(h, cudaEventRecord(h->pev_out[1], st), "event");
+        LM_CUDA(h, cudaStreamWaitEvent(h->cstream, h->pev_out[1], 0), "event wait");
+        if (abundances && !dev_out[0])
+            LM_CUDA(h, cudaMemcpyAsync(abundances, d_x, np * 4, cudaMemcpyDeviceToHost, h->cstream),
+                    "copy x");
+        if (uncertainties && !dev_out[1])
+            LM_CUDA(h, cudaMemcpyAsync(uncertainties, d_sx, np * 4, cudaMemcpyDeviceToHost,
+                                       h->cstream), "copy sx");
+    }
     if (d_rms) LM_CUDA(h, launch_rms(d_cube, h->dS, d_x, N, L, P, d_rms, st), "rms kernel");
     mark(h, 6);
     if (h->opt.profile) ++h->calls;
@@ -665,9 +635,9 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     d_sx = u_sx;
 
     if (!host_any) return LINMIN_OK;
-    if (abundances && !dev_out[0])
+    if (abundances && !dev_out[0] && !early_out)
         LM_CUDA(h, cudaMemcpyAsync(abundances, d_x, np * 4, cudaMemcpyDeviceToHost, st), "copy x");
-    if (uncertainties && !dev_out[1])
+    if (uncertainties && !dev_out[1] && !early_out)
         LM_CUDA(h, cudaMemcpyAsync(uncertainties, d_sx, np * 4, cudaMemcpyDeviceToHost, st), "copy sx");
     if (residual_rms && !dev_out[2])
         LM_CUDA(h, cudaMemcpyAsync(residual_rms, d_rms, (size_t)N * 4, cudaMemcpyDeviceToHost, st),
@@ -675,6 +645,7 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     if (iterations && !dev_out[3])
         LM_CUDA(h, cudaMemcpyAsync(iterations, d_it, (size_t)N * 4, cudaMemcpyDeviceToHost, st),
                 "copy iterations");
+    if (piped) LM_CUDA(h, cudaStreamSynchronize(h->cstream), "output copies");
     return linmin_wait(h, nullptr);
 }
 
@@ -938,7 +909,6 @@ linmin_status lm::destroy_async(linmin_handle h)
         if (h->pev_in[k]) cudaEventDestroy(h->pev_in[k]);
         if (h->pev_out[k]) cudaEventDestroy(h->pev_out[k]);
     }
-    if (h->pinned_cnt) cudaFreeHost(h->pinned_cnt);
     if (h->pool) pool_release(h->device);
     delete h;
     return LINMIN_OK;
