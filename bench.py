@@ -45,6 +45,22 @@ IPM_TRAFFIC = {"ipm_sha256_12": "633fdf1419b5",
                "bytes_per_pixel": (9.679104e6 + 0.087296e6) / 65536}
 
 
+# DRAM bytes of detect_kernel (ncu, 65,536 pixels: 19,948,544 read, 0
+# written; profiles/detect_and_exclude_omega65k.md), valid for the hashed
+# source; traffic grows with the pixel count (rows read once)
+DETECT_TRAFFIC = {"sha256_12": "e16e392227f9", "bytes_per_pixel": 19.948544e6 / 65536}
+
+
+def detect_traffic(n_pix: int):
+    import hashlib
+    src = os.path.join(ROOT, "paper_1402_2518_gb300", "csrc", "detect.cu")
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:12]
+    if h != DETECT_TRAFFIC["sha256_12"]:
+        return None
+    return DETECT_TRAFFIC["bytes_per_pixel"] * n_pix
+
+
 def ipm_traffic(n_pix: int):
     import hashlib
     src = os.path.join(ROOT, "paper_1402_2518_gb300", "csrc", "ipm.cuh")
@@ -468,7 +484,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
             "launches_per_step": 2, "pixels": N,
             "roofline": {"kernel": "detect_kernel", "bound": "hbm", "achieved": gbs,
                          "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "bytes_per_pixel": 8 * P + 24, "traffic": None,
+                         "bytes_per_pixel": 8 * P + 24, "traffic": detect_traffic(N),
                          "l2": f"{flush_gb:g} GiB write before each timed launch"},
             "thresholds": "eq. Threshold from the truth of the cube (population std)",
             "rms_max": rms_max,
