@@ -492,6 +492,14 @@ crossover_pass_kernel(const CrossArgs a)
     const long long n = a.list_in[slot];
     const size_t base = (size_t)n * P;
     const unsigned long long m = a.mask[n];
+    // a large support goes to the lane groups unsolved: its serial chain
+    // here (~k^3 / 3 double-float operations through local memory) would
+    // set the length of the whole pass
+    if (a.defer_k > 0 && a.list_out && __popcll(m) > a.defer_k) {
+        const unsigned long long pos = atomicAdd(a.len_out, 1ULL);
+        a.list_out[pos] = n;
+        return;
+    }
 
     // all arithmetic below is double-float (two float32 words, ~48-bit
     // significand) on the float32 pipes: fp64 is a small fraction of the
@@ -1099,9 +1107,10 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // whole cube: pass 0 one thread per pixel (throughput bound), the
-    // pixels it flips go to list 1; then one launch of lane groups that
-    // takes each listed pixel through up to MAX_SWAPS further support
-    // changes (latency bound, few pixels).  A given list: the lane groups
+    // pixels it flips, and those with more than CROSS_DEFER_K support
+    // coordinates, go to list 1; then one launch of lane groups that takes
+    // each listed pixel through up to MAX_SWAPS + 1 solves (latency bound,
+    // few pixels).  A given list: the lane groups
     // from its first solve, MAX_SWAPS + 1 solves.
     CrossArgs a = base;
     if (!list) {
@@ -1109,11 +1118,13 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
         a.len_in = first_len;
         a.list_out = w.list[1];
         a.len_out = w.len + 1;
+        a.defer_k = CROSS_DEFER_K;
         e = launch_pass(a, st);
         if (e != cudaSuccess) return e;
+        a.defer_k = 0;
         a.list_in = w.list[1];
         a.len_in = w.len + 1;
-        a.max_solves = MAX_SWAPS;
+        a.max_solves = MAX_SWAPS + 1;     // deferred pixels start here
     } else {
         a.list_in = first;
         a.len_in = first_len;
@@ -1127,9 +1138,10 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
 // ------------------------------------------------------------------- rms
 constexpr int RMS_THREADS = 128;
 
-// Grid-stride over pixels, thread per pixel, S^T staged in shared memory
-// once per block; four bands per step (four independent chains over the
-// library, one 16-byte load of the row when rows are 16-byte aligned).
+// Grid-stride over tiles of 2 x RMS_THREADS pixels, a thread takes two
+// pixels (t and t + RMS_THREADS of the tile) so that every S^T value read
+// from shared memory feeds two fits; S^T staged once per block; four bands
+// per step (one 16-byte load of each row when rows are 16-byte aligned).
 template <int NJ4>
 __global__ void __launch_bounds__(RMS_THREADS)
 rms_kernel(const float *__restrict__ cube, const float *__restrict__ S,
@@ -1143,41 +1155,55 @@ rms_kernel(const float *__restrict__ cube, const float *__restrict__ S,
         st[e] = j < P ? S[(size_t)j * L + l] : 0.f;
     }
     __syncthreads();
-    const long long stride = (long long)gridDim.x * RMS_THREADS;
-    for (long long n = (long long)blockIdx.x * RMS_THREADS + threadIdx.x; n < N; n += stride) {
-        float xv[PQ];
+    const long long stride = (long long)gridDim.x * 2 * RMS_THREADS;
+    for (long long t0 = (long long)blockIdx.x * 2 * RMS_THREADS; t0 < N; t0 += stride) {
+        const long long na = t0 + threadIdx.x, nb = na + RMS_THREADS;
+        if (na >= N) continue;                     // nothing left for this thread
+        const bool ha = true, hb = nb < N;
+        // a missing second pixel repeats the first (its result is dropped)
+        const long long ra = na, rb = hb ? nb : ra;
+        float xa[PQ], xb[PQ];
 #pragma unroll
-        for (int j = 0; j < PQ; ++j) xv[j] = j < P ? x[(size_t)n * P + j] : 0.f;
-        const float *y = cube + (size_t)n * L;
-        auto fit = [&](int l) {
+        for (int j = 0; j < PQ; ++j) {
+            xa[j] = j < P ? x[(size_t)ra * P + j] : 0.f;
+            xb[j] = j < P ? x[(size_t)rb * P + j] : 0.f;
+        }
+        const float *ya = cube + (size_t)ra * L, *yb = cube + (size_t)rb * L;
+        auto fit2 = [&](int l, float &ma, float &mb) {
             const float *row = st + (size_t)l * PQ;
-            float m = 0.f;
+            ma = 0.f;
+            mb = 0.f;
 #pragma unroll
             for (int j4 = 0; j4 < NJ4; ++j4) {
                 const float4 sv = *reinterpret_cast<const float4 *>(row + 4 * j4);
-                m = fmaf(xv[4 * j4 + 0], sv.x, m);
-                m = fmaf(xv[4 * j4 + 1], sv.y, m);
-                m = fmaf(xv[4 * j4 + 2], sv.z, m);
-                m = fmaf(xv[4 * j4 + 3], sv.w, m);
+                ma = fmaf(xa[4 * j4 + 0], sv.x, ma); mb = fmaf(xb[4 * j4 + 0], sv.x, mb);
+                ma = fmaf(xa[4 * j4 + 1], sv.y, ma); mb = fmaf(xb[4 * j4 + 1], sv.y, mb);
+                ma = fmaf(xa[4 * j4 + 2], sv.z, ma); mb = fmaf(xb[4 * j4 + 2], sv.z, mb);
+                ma = fmaf(xa[4 * j4 + 3], sv.w, ma); mb = fmaf(xb[4 * j4 + 3], sv.w, mb);
             }
-            return m;
         };
-        float acc0 = 0.f, acc1 = 0.f;
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
         int l = 0;
-        if (vec) {
+        if (vec && ha) {
             for (; l + 4 <= L; l += 4) {
-                const float4 yv = __ldg(reinterpret_cast<const float4 *>(y + l));
-                const float e0 = yv.x - fit(l), e1 = yv.y - fit(l + 1);
-                const float e2 = yv.z - fit(l + 2), e3 = yv.w - fit(l + 3);
-                acc0 = fmaf(e0, e0, acc0); acc1 = fmaf(e1, e1, acc1);
-                acc0 = fmaf(e2, e2, acc0); acc1 = fmaf(e3, e3, acc1);
+                const float4 va = __ldg(reinterpret_cast<const float4 *>(ya + l));
+                const float4 vb = __ldg(reinterpret_cast<const float4 *>(yb + l));
+                float ma, mb;
+                fit2(l, ma, mb);     { const float e = va.x - ma, f = vb.x - mb; a0 = fmaf(e, e, a0); b0 = fmaf(f, f, b0); }
+                fit2(l + 1, ma, mb); { const float e = va.y - ma, f = vb.y - mb; a1 = fmaf(e, e, a1); b1 = fmaf(f, f, b1); }
+                fit2(l + 2, ma, mb); { const float e = va.z - ma, f = vb.z - mb; a0 = fmaf(e, e, a0); b0 = fmaf(f, f, b0); }
+                fit2(l + 3, ma, mb); { const float e = va.w - ma, f = vb.w - mb; a1 = fmaf(e, e, a1); b1 = fmaf(f, f, b1); }
             }
         }
         for (; l < L; ++l) {
-            const float e = __ldg(y + l) - fit(l);
-            acc0 = fmaf(e, e, acc0);
+            float ma, mb;
+            fit2(l, ma, mb);
+            const float e = __ldg(ya + l) - ma, f = __ldg(yb + l) - mb;
+            a0 = fmaf(e, e, a0);
+            b0 = fmaf(f, f, b0);
         }
-        rms[n] = sqrtf((acc0 + acc1) / (float)L);
+        if (ha) rms[na] = sqrtf((a0 + a1) / (float)L);
+        if (hb) rms[nb] = sqrtf((b0 + b1) / (float)L);
     }
 }
 
@@ -1189,7 +1215,7 @@ static cudaError_t launch_rms_t(const float *cube, const float *S, const float *
     cudaError_t e = cudaFuncSetAttribute(rms_kernel<NJ4>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const unsigned blocks = persistent_blocks(rms_kernel<NJ4>, RMS_THREADS, smem, N);
+    const unsigned blocks = persistent_blocks(rms_kernel<NJ4>, RMS_THREADS, smem, (N + 1) / 2);
     rms_kernel<NJ4><<<blocks, RMS_THREADS, smem, st>>>(cube, S, x, N, L, P, rms,
                                                       rows_aligned(cube, L));
     return cudaGetLastError();
