@@ -492,15 +492,6 @@ crossover_pass_kernel(const CrossArgs a)
     const long long n = a.list_in[slot];
     const size_t base = (size_t)n * P;
     const unsigned long long m = a.mask[n];
-    // a large support goes to the lane groups unsolved: its serial chain
-    // here (~k^3 / 3 double-float operations through local memory) would
-    // set the length of the whole pass
-    if (a.defer_k > 0 && a.list_out && __popcll(m) > a.defer_k) {
-        const unsigned long long pos = atomicAdd(a.len_out, 1ULL);
-        a.list_out[pos] = n;
-        return;
-    }
-
     // all arithmetic below is double-float (two float32 words, ~48-bit
     // significand) on the float32 pipes: fp64 is a small fraction of the
     // fp32 rate on this GPU
@@ -1107,10 +1098,9 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // whole cube: pass 0 one thread per pixel (throughput bound), the
-    // pixels it flips, and those with more than CROSS_DEFER_K support
-    // coordinates, go to list 1; then one launch of lane groups that takes
-    // each listed pixel through up to MAX_SWAPS + 1 solves (latency bound,
-    // few pixels).  A given list: the lane groups
+    // pixels it flips go to list 1; then one launch of lane groups that
+    // takes each listed pixel through up to MAX_SWAPS further support
+    // changes (latency bound, few pixels).  A given list: the lane groups
     // from its first solve, MAX_SWAPS + 1 solves.
     CrossArgs a = base;
     if (!list) {
@@ -1118,13 +1108,11 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
         a.len_in = first_len;
         a.list_out = w.list[1];
         a.len_out = w.len + 1;
-        a.defer_k = CROSS_DEFER_K;
         e = launch_pass(a, st);
         if (e != cudaSuccess) return e;
-        a.defer_k = 0;
         a.list_in = w.list[1];
         a.len_in = w.len + 1;
-        a.max_solves = MAX_SWAPS + 1;     // deferred pixels start here
+        a.max_solves = MAX_SWAPS;
     } else {
         a.list_in = first;
         a.len_in = first_len;

@@ -18,10 +18,6 @@ constexpr int MAX_SWAPS = 8;
 // 1e-11 they are the ones the crossover would drop again): ~10% of pixels
 // then need a support change instead of ~40% with 1.
 constexpr float SUPPORT_THETA = 0.01f;
-// The first crossover solve of a pixel whose support has more coordinates
-// than this runs in the lane groups instead of one thread (2% of the
-// OMEGA-shaped pixels; their serial chains otherwise set the pass's length).
-constexpr int CROSS_DEFER_K = 14;
 
 // Bucket of the interior-point kernel for a library size P.
 struct Bucket { int NS, G, PP; };
@@ -117,8 +113,6 @@ struct CrossArgs {
     int *it_mark;                  // with n_unverified: iteration counts, negated
                                    // (not converged) for a pixel left unverified
     int max_solves;                // lane-group kernel: support solves per pixel
-    int defer_k;                   // thread pass: supports larger than this go
-                                   // to list_out unsolved (0: none)
     double tol_x, tol_g;
 };
 
