@@ -80,7 +80,7 @@ struct linmin_ctx {
     cudaMemPool_t pool = nullptr; // device memory of this handle (see pool_acquire)
     // host-buffer pipeline: copy stream and its events
     cudaStream_t cstream = nullptr;
-    cudaEvent_t pev_in[4] = {}, pev_out[4] = {};
+    cudaEvent_t pev_in[8] = {}, pev_out[2] = {};
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -434,7 +434,7 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
 // copy stream, the projection of each piece starts as soon as it has
 // arrived (the copy of the next piece overlaps it); with host outputs, x
 // and sigma_x go back on the copy stream while the RMS runs.
-constexpr int PIPE_CHUNKS = 4;
+constexpr int PIPE_CHUNKS = 8;
 constexpr long long PIPE_MIN_N = 65536;
 
 static linmin_status ensure_copy_stream(linmin_ctx *h)
@@ -905,10 +905,10 @@ linmin_status lm::destroy_async(linmin_handle h)
         cudaStreamSynchronize(h->cstream);
         cudaStreamDestroy(h->cstream);
     }
-    for (int k = 0; k < 4; ++k) {
-        if (h->pev_in[k]) cudaEventDestroy(h->pev_in[k]);
-        if (h->pev_out[k]) cudaEventDestroy(h->pev_out[k]);
-    }
+    for (cudaEvent_t e : h->pev_in)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->pev_out)
+        if (e) cudaEventDestroy(e);
     if (h->pool) pool_release(h->device);
     delete h;
     return LINMIN_OK;

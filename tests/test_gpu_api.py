@@ -81,7 +81,7 @@ def test_autotune_and_lanes():
 
 def test_host_buffers_pipelined_equal_device():
     """Host buffers of at least 65,536 pixels go through the copy/compute
-    pipeline (four pieces, copies on their own stream): the results equal
+    pipeline (eight pieces, copies on their own stream): the results equal
     the device-pointer call bit for bit, with a ragged last piece and a
     missing output."""
     import paper_1402_2518_gb300 as pkg
