@@ -100,6 +100,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(v: float, dist=None, device="cpu") -> float:
+    """The largest v over the ranks of the process group (v itself without
+    one): the timing of a step is that of its slowest replica."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(v)
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(n_local: int, seconds: float, world_size: int) -> float:
+    """Whole-job throughput of identical replicas (weak scaling): every rank
+    unmixes its own cube of n_local pixels in at most `seconds`."""
+    return n_local * world_size / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -558,9 +575,7 @@ def main():
             phase_tot[k] += v * args.steps / n_phase
     launches = pkg.linmin_last_launches(um.h)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         dist.barrier()
     st, nbad = um.wait()
 
@@ -569,10 +584,8 @@ def main():
     if not args.no_e2e:
         e2e_s = run_e2e(pkg, cube, max(3, args.steps // 2), prec)
         if ws > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": N * ws / e2e_s, "unit": "pixels/s",
+            e2e_s = max_over_ranks(e2e_s, dist, dev)
+        e2e = {"value": replicas_value(N, e2e_s, ws), "unit": "pixels/s",
                "h2d_bytes_per_step": N * L * 4 + L * 4,
                "d2h_bytes_per_step": N * (2 * P + 2) * 4}
     full_cov = None
@@ -594,7 +607,7 @@ def main():
         dist.barrier() if ws > 1 else None
         return
 
-    value = N * ws / (ms / 1e3)
+    value = replicas_value(N, ms / 1e3, ws)
     peaks = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     nsm = props.multi_processor_count
