@@ -578,25 +578,12 @@ crossover_pass_kernel(const CrossArgs a)
         }
         if (flip >= 0 && k == 1) flip = -2;       // cannot drop the last one
         if (flip == -1) {
-            // most negative multiplier off S.  A float32 screen first: a
-            // multiplier whose float32 value exceeds its rounding bound
-            // (1e-5 of the magnitudes summed, far above the float32 error
-            // of a k-term dot product) is positive, so it can be neither
-            // the most negative one nor below -tol_g; the others get the
-            // double-float dot product, four coordinates at once
+            // most negative multiplier off S; four coordinates at once
             float lmin = (float)-a.tol_g;
             int off[KMAX];
             int noff = 0;
-            for (int i = 0; i < P; ++i) {
-                if ((m >> i) & 1ULL) continue;
-                float g = nu.hi - a.c_hi[base + i], mag = fabsf(nu.hi) + fabsf(a.c_hi[base + i]);
-                for (int q = 0; q < k; ++q) {
-                    const float t = sGh[i * P + idx[q]] * xs[q].hi;
-                    g += t;
-                    mag += fabsf(t);
-                }
-                if (!(g > 1e-5f * mag)) off[noff++] = i;
-            }
+            for (int i = 0; i < P; ++i)
+                if (!((m >> i) & 1ULL)) off[noff++] = i;
             for (int o = 0; o < noff; o += 4) {
                 int ii[4];
                 dot2 g[4];
