@@ -301,6 +301,12 @@ linmin_status linmin_create(const float *library, int L, int P, const linmin_opt
     (*out)->user_P = P;
     (*out)->slack = true;
     (*out)->slack_scale = M;
+    if (o.constraint == LINMIN_POS) {
+        // start at abundances 1/P in the caller's units (sum 1 against the
+        // bound M): x' = 1/(M P) on the spectra, the rest on the slack
+        (*out)->prep.slack_idx = P;
+        (*out)->prep.slack_x0 = 1.f - 1.f / M;
+    }
     return LINMIN_OK;
 }
 
@@ -338,6 +344,7 @@ static IpmArgs ipm_args(linmin_ctx *h, long long N)
     ia.N = N; ia.P = h->P; ia.max_iter = h->opt.max_iter;
     ia.c_hi = h->c_hi; ia.c_lo = h->c_lo;
     ia.Ghi = h->prep.Ghi; ia.Glo = h->prep.Glo; ia.grs = h->prep.grs;
+    ia.slack_idx = h->prep.slack_idx; ia.slack_x0 = h->prep.slack_x0;
     ia.x_state = h->x; ia.lam_state = h->lam; ia.nu_state = h->nu; ia.it_state = h->it;
     ia.n_notconv = h->dcnt + 2;
     // pos works on M S, whose coordinates are M times smaller: the absolute

@@ -53,7 +53,9 @@ struct IpmArgs {
     int max_iter;
     const float *c_hi, *c_lo;      // N x P, scaled projection c~ (hi + lo)
     const float *Ghi, *Glo;        // PP x PP row-major, zero padded (G~ hi + lo)
-    const float *grs;              // PP: G~ (1/P) 1, the gradient term at x0 = 1/P
+    const float *grs;              // PP: G~ x0, the gradient term at the start x0
+    int slack_idx = -1;            // x0: 1/P, or slack_x0 on slack_idx and
+    float slack_x0 = 0.f;          //     (1 - slack_x0) / (P - 1) elsewhere
     float *x_state, *lam_state;    // N x P
     float *nu_state;               // N
     int *it_state;                 // N: iterations so far (phase A) / final (phase B, <0: cap)
@@ -126,6 +128,7 @@ ipm_kernel(const IpmArgs a)
 
     const int P = a.P;
     const float invP = 1.0f / (float)P;
+    const float x0o = a.slack_idx >= 0 ? (1.0f - a.slack_x0) / (float)(P - 1) : invP;
     bool valid[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) valid[s] = s * G + t < P;
@@ -151,7 +154,7 @@ ipm_kernel(const IpmArgs a)
         const size_t base = (size_t)p * P;
         cbase = base;
         if (!ACC) {
-            // x0 = 1/P; g0 = G~ x0 - c~; nu0 makes lambda0 = g0 + nu0 dual
+            // x0 (1/P, or the slack start); g0 = G~ x0 - c~; nu0 makes lambda0 = g0 + nu0 dual
             // feasible with min lambda0 = 1e-3 (a smaller start than adding
             // the spread of g0 as well: 11.2 instead of 11.7 iterations on
             // the OMEGA-shaped workload)
@@ -166,7 +169,7 @@ ipm_kernel(const IpmArgs a)
             nu = 1e-3f - gmin;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                x[s] = valid[s] ? invP : 0.f;
+                x[s] = valid[s] ? (s * G + t == a.slack_idx ? a.slack_x0 : x0o) : 0.f;
                 lam[s] = valid[s] ? g0[s] + nu : 0.f;
             }
             it = 0;

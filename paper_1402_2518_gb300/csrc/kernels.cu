@@ -50,8 +50,10 @@ __global__ void prep_gram_kernel(const float *__restrict__ S, const float *__res
 __global__ void prep_finish_kernel(int P, int PP, const double *__restrict__ G64,
                                    double *__restrict__ Gt64, double *__restrict__ scale,
                                    float *__restrict__ Ghi, float *__restrict__ Glo,
-                                   float *__restrict__ grs, float *__restrict__ gdiag, int *flags)
+                                   float *__restrict__ grs, float *__restrict__ gdiag, int *flags,
+                                   int slack_idx, float slack_x0)
 {
+    const double x0o = slack_idx >= 0 ? (1.0 - (double)slack_x0) / (P - 1) : 1.0 / P;
     __shared__ double s_sh;
     if (threadIdx.x == 0) {
         double tr = 0.0;
@@ -77,8 +79,8 @@ __global__ void prep_finish_kernel(int P, int PP, const double *__restrict__ G64
     for (int i = threadIdx.x; i < PP; i += blockDim.x) {
         double r = 0.0;
         if (i < P) {
-            for (int j = 0; j < P; ++j) r += G64[(size_t)i * P + j] / s + RHO;
-            r /= P;
+            for (int j = 0; j < P; ++j)
+                r += (G64[(size_t)i * P + j] / s + RHO) * (j == slack_idx ? (double)slack_x0 : x0o);
             // curvature of the support test; a zero spectrum (the slack of
             // the sum <= 1 constraint) has none: unit curvature there
             const double gi = G64[(size_t)i * P + i] / s;
@@ -115,7 +117,7 @@ cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP
     const int threads = 256, wpb = threads / 32;
     prep_gram_kernel<<<(npairs + wpb - 1) / wpb, threads, 0, st>>>(S, sigma, L, P, o.G64, o.flags);
     prep_finish_kernel<<<1, 256, 0, st>>>(P, PP, o.G64, o.Gt64, o.scale, o.Ghi, o.Glo,
-                                          o.grs, o.gdiag, o.flags);
+                                          o.grs, o.gdiag, o.flags, o.slack_idx, o.slack_x0);
     const int PQ = pq_of(P);
     const long long total = (long long)L * PQ;
     const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
@@ -292,7 +294,7 @@ cudaError_t launch_prep_cov(const float *S, const double *Cinv, int L, int P, in
     const int threads = 256, wpb = threads / 32;
     prep_gram_cov_kernel<<<(npairs + wpb - 1) / wpb, threads, 0, st>>>(S, T, L, P, o.G64);
     prep_finish_kernel<<<1, 256, 0, st>>>(P, PP, o.G64, o.Gt64, o.scale, o.Ghi, o.Glo,
-                                          o.grs, o.gdiag, o.flags);
+                                          o.grs, o.gdiag, o.flags, o.slack_idx, o.slack_x0);
     const int PQ = pq_of(P);
     const long long total = (long long)L * PQ;
     const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);

@@ -33,10 +33,14 @@ struct Prep {
     double *Gt64;    // P x P   G~ = G / s + rho (fp64)
     double *scale;   // 1       s = trace(G) / P
     float *Ghi, *Glo;// PP x PP G~ as hi + lo float32, zero padded
-    float *grs;      // PP      G~ 1 / P
+    float *grs;      // PP      G~ x0 (the gradient term at the start point)
     float *gdiag;    // P       diag(G) / s
     float *Bhi, *Blo;// L x PQ  W^2 S^T / s as hi + lo float32, [l][j]
     int *flags;      // 1       bit 0: invalid sigma, bit 1: bad scale
+    // interior-point start x0: 1/P everywhere, or (slack_idx >= 0) slack_x0
+    // on that coordinate and (1 - slack_x0) / (P - 1) on the others
+    int slack_idx = -1;
+    float slack_x0 = 0.f;
 };
 
 // kernel launches issued by launch_prep and launch_crossover (kept next to
