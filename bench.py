@@ -41,8 +41,8 @@ FP32_LANES_PER_SM = 128
 # (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels; traffic
 # grows with the pixel count).  Valid only for the kernel source it was
 # measured on (hash of csrc/ipm.cuh).
-IPM_TRAFFIC = {"ipm_sha256_12": "633fdf1419b5",
-               "bytes_per_pixel": (9.679104e6 + 0.087296e6) / 65536}
+IPM_TRAFFIC = {"ipm_sha256_12": "a8ebf479dc4e",
+               "bytes_per_pixel": (9.524992e6 + 0.027648e6) / 65536}
 
 
 # DRAM bytes of detect_kernel (ncu, 65,536 pixels: 19,948,544 read, 0
