@@ -359,17 +359,18 @@ LINMIN_API linmin_status linmin_server_destroy(linmin_server s);
  * an integration entry point, not part of the method.
  *
  *   library, cube, sigma, outputs: as in linmin_create/linmin_unmix, but
- *            every non-NULL pointer must be device memory (else
- *            LINMIN_ERR_INVALID);
+ *            every non-NULL pointer must be device memory of the current
+ *            device, or managed memory (else LINMIN_ERR_INVALID);
  *   cuda_stream: the cudaStream_t to run on (NULL: default stream); the
  *            call queues its work and returns without synchronising.
  * Limit: the scratch needed is, with every piece rounded up to 256 bytes,
  *   2 P^2 doubles + 1 double + 2 PP^2 + PP + P + 2 L*PQ floats + 1 int
  *   + 20 + P uint64 + P + 1 uint32 + N (4 P + 11) 4-byte words
  *   <=  LINMIN_NOALLOC_SCRATCH_MB MiB
- *   (PP = P rounded up to the kernel bucket 8, 16, 32, 40 or 48; PQ = P
- *   rounded up to a multiple of 4); for L = 184, P = 36 that is about
- *   107,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any work.
+ *   (PP = P rounded up to the kernel bucket 8, 16, 32, 36, 40, 48 or 64;
+ *   PQ = P rounded up to a multiple of 4); for L = 184, P = 36 that is
+ *   about 107,000 pixels.  A larger N returns LINMIN_ERR_INVALID before any
+ *   work (linmin_noalloc_scratch_bytes gives the figure for a size).
  * Unlike linmin_create it does not check rank [S^T; 1^T] = P: the caller
  *   guarantees a library whose constrained minimiser is unique.
  * Set-up: the first call on a device looks up the array's device address
@@ -380,12 +381,26 @@ LINMIN_API linmin_status linmin_server_destroy(linmin_server s);
  *   call).  Calls whose work overlaps on the GPU (different streams, or
  *   different host threads) race on it: serialise them on one stream.
  * Non-converged pixels are reported by iterations < 0 only.
+ * Invalid inputs found on the device: the call returns before its work
+ *   has run, so a sigma with a value that is not finite or not > 0, or a
+ *   library whose whitened Gram has a zero trace, cannot change the status
+ *   it returns.  Instead every output of that call is marked: abundances,
+ *   uncertainties and RMS are NaN and every iteration count is INT_MIN.
  */
 LINMIN_API linmin_status linmin_unmix_noalloc(const float *library, int L, int P,
                                               const float *cube, long long N,
                                               const float *sigma, float *abundances,
                                               float *uncertainties, float *residual_rms,
                                               int *iterations, void *cuda_stream);
+
+/* Device bytes linmin_unmix_noalloc needs for (L, P, N), in *bytes
+ * (host pointer; set to 0 on failure).  Returns LINMIN_OK when they fit in
+ * the LINMIN_NOALLOC_SCRATCH_MB array, LINMIN_ERR_INVALID when they do not
+ * (or N < 0, L out of range) and LINMIN_ERR_UNSUPPORTED for P outside
+ * 1..LINMIN_MAX_P.  Host arithmetic only: no device call.  The paper has no
+ * counterpart. */
+LINMIN_API linmin_status linmin_noalloc_scratch_bytes(int L, int P, long long N,
+                                                      unsigned long long *bytes);
 
 /* ------------------------------------------------------------------ */
 /*

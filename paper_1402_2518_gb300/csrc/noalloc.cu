@@ -8,6 +8,7 @@
 // with cudaGetSymbolAddress (first call on that device) and cached.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <mutex>
 
 #include "ipm.cuh"
@@ -45,23 +46,36 @@ cudaError_t scratch_address(void **out)
     return cudaSuccess;
 }
 
-// Bump allocator over the scratch array (256-byte aligned pieces).
+// Bump allocator over the scratch array (256-byte aligned pieces).  A
+// piece that does not fit within cap sets ok = false (and returns the
+// base, never an address past the array).
 struct Carve {
     unsigned char *base;
     size_t off = 0, cap;
+    bool ok = true;
     template <typename T>
     T *take(size_t n)
     {
-        off = (off + 255) & ~(size_t)255;
-        T *p = reinterpret_cast<T *>(base + off);
-        off += (n ? n : 1) * sizeof(T);
-        return p;
+        if (n == 0) n = 1;
+        const size_t start = (off + 255) & ~(size_t)255;
+        if (start < off || start > cap || n > (cap - start) / sizeof(T)) {
+            ok = false;
+            return reinterpret_cast<T *>(base);
+        }
+        off = start + n * sizeof(T);
+        return reinterpret_cast<T *>(base + start);
     }
 };
 
+// Every per-pixel piece holds at least 4 (4 P + 11) bytes per pixel, so a
+// larger N cannot fit: refused before any size arithmetic can overflow.
+long long coarse_max_pixels(int P) { return (long long)(NOALLOC_BYTES / (4 * (4 * (size_t)P + 11))); }
+
+// Bytes the call needs (rounded pieces), or 0 when they exceed the array.
 size_t scratch_needed(int L, int P, int PP, long long N)
 {
-    Carve c{nullptr, 0, 0};
+    if (N > coarse_max_pixels(P)) return 0;
+    Carve c{nullptr, 0, NOALLOC_BYTES};
     const int PQ = pq_of(P);
     c.take<double>((size_t)P * P);
     c.take<double>((size_t)P * P);
@@ -86,15 +100,38 @@ size_t scratch_needed(int L, int P, int PP, long long N)
     c.take<long long>(N);
     c.take<long long>(N);
     c.take<int>(N);
-    return c.off;
+    return c.ok ? c.off : 0;
 }
 
-bool is_device(const void *p)
+// Device memory of the current device (or managed memory).  Memory of
+// another GPU is refused: the kernels run on the current one.
+bool is_device(const void *p, int dev)
 {
     if (!p) return true;   // NULL outputs are allowed
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// When the preparation flagged sigma (non-finite or <= 0) or the library
+// (zero whitened scale), every output of the call is marked: NaN
+// abundances, uncertainties and RMS, iteration counts INT_MIN.
+__global__ void noalloc_mark_invalid_kernel(const int *flags, long long N, int P, float *x,
+                                            float *sx, float *rms, int *it)
+{
+    if (*flags == 0) return;
+    const float nan = __int_as_float(0x7fc00000);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = first; i < N * P; i += stride) {
+        if (x) x[i] = nan;
+        if (sx) sx[i] = nan;
+    }
+    for (long long i = first; i < N; i += stride) {
+        if (rms) rms[i] = nan;
+        if (it) it[i] = INT_MIN;
+    }
 }
 
 }  // namespace
@@ -112,9 +149,12 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     if (L < P || L > LINMIN_MAX_L) return LINMIN_ERR_INVALID;
     if (N == 0) return LINMIN_OK;
     // beyond the static array: refuse (limit stated with LINMIN_NOALLOC_SCRATCH_MB)
-    if (scratch_needed(L, P, b.PP, N) > NOALLOC_BYTES) return LINMIN_ERR_INVALID;
-    if (!is_device(library) || !is_device(cube) || !is_device(sigma) || !is_device(abundances) ||
-        !is_device(uncertainties) || !is_device(residual_rms) || !is_device(iterations))
+    if (scratch_needed(L, P, b.PP, N) == 0) return LINMIN_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LINMIN_ERR_CUDA;
+    if (!is_device(library, dev) || !is_device(cube, dev) || !is_device(sigma, dev) ||
+        !is_device(abundances, dev) || !is_device(uncertainties, dev) ||
+        !is_device(residual_rms, dev) || !is_device(iterations, dev))
         return LINMIN_ERR_INVALID;
     void *base = nullptr;
     cudaError_t e = scratch_address(&base);
@@ -150,6 +190,7 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     xw.list[0] = c.take<long long>(N);
     xw.list[1] = c.take<long long>(N);
     xw.ksize = c.take<int>(N);
+    if (!c.ok) return LINMIN_ERR_INVALID;   // cannot happen after scratch_needed
 
 #define NA_CUDA(call)                                  \
     do {                                               \
@@ -192,7 +233,22 @@ linmin_status linmin_unmix_noalloc(const float *library, int L, int P, const flo
     if (iterations)
         NA_CUDA(cudaMemcpyAsync(iterations, its, (size_t)N * sizeof(int),
                                 cudaMemcpyDeviceToDevice, st));
+    noalloc_mark_invalid_kernel<<<152 * 4, 256, 0, st>>>(pr.flags, N, P, abundances,
+                                                         uncertainties, residual_rms, iterations);
+    NA_CUDA(cudaGetLastError());
 #undef NA_CUDA
+    return LINMIN_OK;
+}
+
+linmin_status linmin_noalloc_scratch_bytes(int L, int P, long long N, unsigned long long *bytes)
+{
+    if (bytes) *bytes = 0;
+    Bucket b;
+    if (P < 1 || P > LINMIN_MAX_P || !ipm_bucket(P, &b)) return LINMIN_ERR_UNSUPPORTED;
+    if (N < 0 || L < P || L > LINMIN_MAX_L) return LINMIN_ERR_INVALID;
+    const size_t need = scratch_needed(L, P, b.PP, N);
+    if (need == 0) return LINMIN_ERR_INVALID;
+    if (bytes) *bytes = need;
     return LINMIN_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
             "linmin_thresholds", "linmin_autofit", "linmin_second_pass",
-            "linmin_unmix_masked")
+            "linmin_unmix_masked", "linmin_noalloc_scratch_bytes")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -130,6 +130,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_unmix_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_longlong,
                                          P, P, P, P, P, ctypes.c_void_p]
     lib.linmin_unmix_noalloc.restype = ctypes.c_int
+    lib.linmin_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                                 ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.linmin_noalloc_scratch_bytes.restype = ctypes.c_int
     SV = ctypes.c_void_p
     lib.linmin_server_default_options.argtypes = [ctypes.POINTER(linmin_server_options)]
     lib.linmin_server_default_options.restype = ctypes.c_int
@@ -297,6 +300,13 @@ def linmin_unmix_noalloc(library, L: int, P: int, cube, N: int, sigma, abundance
     return lib().linmin_unmix_noalloc(_ptr(library), int(L), int(P), _ptr(cube), int(N),
                                       _ptr(sigma), _ptr(abundances), _ptr(uncertainties),
                                       _ptr(residual_rms), _ptr(iterations, "int32"), st)
+
+
+def linmin_noalloc_scratch_bytes(L: int, P: int, N: int) -> tuple[int, int]:
+    """(status, bytes) of linmin_unmix_noalloc's scratch for (L, P, N)."""
+    b = ctypes.c_ulonglong(0)
+    st = lib().linmin_noalloc_scratch_bytes(int(L), int(P), int(N), ctypes.byref(b))
+    return st, int(b.value)
 
 
 def linmin_get_lanes(h) -> int:

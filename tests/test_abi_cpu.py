@@ -180,3 +180,30 @@ def test_constraint_rank_refusal_on_host():
     opt.constraint = 7
     assert lib.linmin_create(cube.S.ctypes.data_as(ctypes.c_void_p), cube.L, cube.P,
                              ctypes.byref(opt), ctypes.byref(h)) == linmin.LINMIN_ERR_UNSUPPORTED
+
+
+def test_noalloc_size_bound_on_host():
+    """The scratch-size arithmetic of linmin_unmix_noalloc cannot wrap: N far
+    beyond the array (up to 2^62, where a product N * (4P + 11) * 4 would
+    overflow 64 bits) is refused, and the figure for a size that fits is
+    consistent with the documented per-pixel cost.  Host arithmetic only."""
+    st, b = pkg.linmin_noalloc_scratch_bytes(184, 36, 1 << 62)
+    assert st == linmin.LINMIN_ERR_INVALID and b == 0
+    st, b = pkg.linmin_noalloc_scratch_bytes(184, 32, (1 << 64) // (4 * (4 * 32 + 11)) + 1)
+    assert st == linmin.LINMIN_ERR_INVALID
+    st, b1 = pkg.linmin_noalloc_scratch_bytes(184, 36, 100000)
+    st2, b2 = pkg.linmin_noalloc_scratch_bytes(184, 36, 100001)
+    assert st == st2 == linmin.LINMIN_OK
+    assert 4 * (4 * 36 + 11) <= b2 - b1 <= 4 * (4 * 36 + 11) + 11 * 256
+    cap = linmin.LINMIN_NOALLOC_SCRATCH_MB << 20
+    assert b1 <= cap
+    # the largest N that fits, and the first that does not
+    lo, hi = 1, cap
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        ok = pkg.linmin_noalloc_scratch_bytes(184, 36, mid)[0] == linmin.LINMIN_OK
+        lo, hi = (mid, hi) if ok else (lo, mid)
+    assert 100000 < lo < 110000
+    assert pkg.linmin_noalloc_scratch_bytes(184, 36, hi)[0] == linmin.LINMIN_ERR_INVALID
+    assert pkg.linmin_noalloc_scratch_bytes(184, 65, 10)[0] == linmin.LINMIN_ERR_UNSUPPORTED
+    assert pkg.linmin_noalloc_scratch_bytes(184, 36, -1)[0] == linmin.LINMIN_ERR_INVALID
