@@ -50,9 +50,25 @@ def run_gpu(pkg, S, sigma, X, **kw):
 
 
 def unambiguous(ref, S, sigma):
+    """Pixels whose support is resolved by the data (reading of the
+    uncertainty definition, Sec. 2.3: the covariance is taken on the support
+    of the solution, which strict complementarity must fix).  A coordinate
+    is ambiguous when lambda_i / (x_i G_ii) lies in [1e-3, 1e3], or when
+    its margin, in the scaled units of the solver (G / s, s = trace(G) / P),
+    is below 1e-8: for an inactive coordinate the margin is its multiplier
+    lambda_i, for an active one the multiplier that dropping it would leave,
+    x_i / sigma_i^2 (the diagonal of the bordered inverse is sigma^2).  A
+    margin below 1e-8 is within 10x of the exactness stage's acceptance
+    tolerance and below the ~6e-8 relative rounding of float32 input data,
+    so either support is consistent with the data."""
     G, _ = _pins.whiten(S, sigma)
-    ratio = ref["lam"] / np.maximum(ref["x"], 1e-300) / np.diag(G)[None, :]
-    return ~np.any((ratio > 1e-3) & (ratio < 1e3), axis=1)
+    s = np.trace(G) / G.shape[0]
+    x, lam = ref["x"], ref["lam"]
+    ratio = lam / np.maximum(x, 1e-300) / np.diag(G)[None, :]
+    active = ratio < 1e-3
+    with np.errstate(divide="ignore"):
+        margin = np.where(active, x / np.maximum(ref["sx"], 1e-300) ** 2, lam) / s
+    return ~np.any((ratio > 1e-3) & (ratio < 1e3), axis=1) & np.all(margin >= 1e-8, axis=1)
 
 
 def check(gpu, ref, S, sigma, X, rows=None):
