@@ -413,7 +413,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
                   n_second: bool = True, flush_gb: float = 4.0):
     """Detection products on the unmixed cube: eq. Threshold from the known
     truth (threshold sums kernel), then the per-pixel detection kernel with
-    the three conditions of Sec. 5.  Each detection launch is timed alone
+    the three conditions of Sec. 4.  Each detection launch is timed alone
     with events on its stream, after a 4 GiB write that flushes L2 (its
     inputs, 8P + 24 bytes per pixel, fit in L2)."""
     import ctypes
@@ -455,7 +455,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
     torch.cuda.synchronize()
     d = pkg.detection_summary(out)
     nt = int(d["n_true"][:nm].sum())
-    # library auto-fit (Sec. 2.5), one call
+    # library auto-fit (Sec. 2.4), one call
     S = torch.from_numpy(cube.S).to(dev)
     rl = torch.empty((P, cube.L), device=dev); rn = torch.empty((P, cube.L), device=dev)
     a0 = torch.cuda.Event(enable_timing=True); a1 = torch.cuda.Event(enable_timing=True)
@@ -466,7 +466,7 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
     a1.record(stream)
     torch.cuda.synchronize()
     autofit_ms = a0.elapsed_time(a1)
-    # second pass (Sec. 6): every pixel unmixed again with its detected
+    # second pass (Sec. 5): every pixel unmixed again with its detected
     # minerals and the extras (linmin_unmix_masked, K calls timed on the
     # stream like the main step)
     second = None

@@ -405,7 +405,7 @@ LINMIN_API linmin_status linmin_noalloc_scratch_bytes(int L, int P, long long N,
 /* ------------------------------------------------------------------ */
 /*
  * Detection products.  After unmixing, a mineral counts as detected in a
- * pixel under the conditions the paper lists for real images (Sec. 5,
+ * pixel under the conditions the paper lists for real images (Sec. 4,
  * introduction): its abundance is above a threshold chosen per mineral,
  * its uncertainty is below its abundance, and the pixel's RMS is below
  * the noise level.  The thresholds come from the synthetic surface
@@ -491,7 +491,7 @@ LINMIN_API linmin_status linmin_threshold_stats(const float *x, const unsigned l
 LINMIN_API linmin_status linmin_thresholds(const linmin_threshold_sums *stats, int n_minerals,
                                            float *c_out);
 
-/* Auto-fit of the library (Sec. 2.5, "Estimation of degeneracies"): each
+/* Auto-fit of the library (Sec. 2.4, "Estimation of degeneracies"): each
  * spectrum S_n is fitted by the P - 1 others, S_n = A'.S' + E, without
  * constraints and with A' >= 0, to show which spectra the others can
  * mimic.  Unweighted, fp64 on the device, one block per n.
@@ -517,7 +517,7 @@ LINMIN_API linmin_status linmin_autofit(const float *library, int L, int P, floa
  * columns j < n_minerals whose bit j is set in mask[n] and every column
  * j >= n_minerals (the additional spectra), as if it were unmixed with
  * that sub-library alone; the abundances and uncertainties of its
- * left-out columns are 0.  This is the second pass of Sec. 6 (mask: the
+ * left-out columns are 0.  This is the second pass of Sec. 5 (mask: the
  * detections of linmin_detect).  Arguments as linmin_unmix; mask is
  * device memory (N bit masks, bits >= n_minerals ignored);
  * 0 <= n_minerals < P (for SLO / POS handles: the caller's P).
@@ -533,7 +533,7 @@ LINMIN_API linmin_status linmin_unmix_masked(linmin_handle h, const float *cube,
                                              float *uncertainties, float *residual_rms,
                                              int *iterations);
 
-/* Second pass (Sec. 6) in one call: a handle for the full library
+/* Second pass (Sec. 5) in one call: a handle for the full library
  * (host or device, P x L, minerals first: columns < n_minerals; rank
  * checked as in linmin_create, and then every subset of its columns gives
  * a unique minimiser too), linmin_unmix_masked with the detection masks,

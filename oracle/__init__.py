@@ -69,6 +69,14 @@ def _load():
             lib.oracle_unmix.argtypes = [ctypes.c_int, ctypes.c_int, F, F,
                                          ctypes.c_longlong, F, ctypes.c_int,
                                          ctypes.c_int, D, D, D, I, D, D, D, I, I]
+            lib.oracle_unmix_set.argtypes = [ctypes.c_int, ctypes.c_int, F, F,
+                                             ctypes.c_longlong, F, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, D, D, D, I, D, D, D, I, I, D, D]
+            lib.oracle_pos.argtypes = [ctypes.c_int, D, D, ctypes.c_double, ctypes.c_int,
+                                       D, D, I, D]
+            lib.oracle_slo.argtypes = [ctypes.c_int, D, D, ctypes.c_double, ctypes.c_int,
+                                       D, D, D, D, I, D]
+            lib.oracle_sigma_x_set.argtypes = [ctypes.c_int, D, I, ctypes.c_int, D]
             _lib = lib
     return _lib
 
@@ -185,45 +193,79 @@ def unmix(S, sigma, X, nthreads: int = 0, max_iter: int = MAX_ITER,
     return out
 
 
-POS_SCALE = 64.0
+CONSTRAINTS = {"sto": 0, "slo": 1, "pos": 2}
 
 
-def unmix_constraint(S, sigma, X, constraint: str = "sto", max_iter: int = MAX_ITER):
-    """Unmixing under the constraint sets of the paper (Sec. 2.2): "sto"
-    x >= 0, sum x = 1 (``unmix``); "slo" x >= 0, sum x <= 1; "pos" x >= 0.
+def unmix_constraint(S, sigma, X, constraint: str = "sto", max_iter: int = MAX_ITER,
+                     nthreads: int = 0):
+    """Unmixing under the constraint sets of the paper (Sec. 2.2 and the runs
+    of Sec. 4): "sto" x >= 0, sum x = 1 (``unmix``); "slo" x >= 0,
+    sum x <= 1 (``oracle_slo``: the inequality with its slack w and
+    multiplier omega); "pos" x >= 0 alone (``oracle_pos``: no bound on the
+    sum).  The uncertainty is the support-restricted inverse Hessian,
+    bordered by the sum constraint only where it is active (slo: omega > w).
 
-    slo is the sum-to-one problem on the library with a zero spectrum
-    appended: its coefficient w = 1 - sum x >= 0 is the slack of the
-    inequality and adds nothing to the fit, so the two problems have the
-    same minimiser.  pos is slo on POS_SCALE S (x = POS_SCALE x'), the same
-    as pos whenever sum x < POS_SCALE (pixels where the bound is reached get
-    negative iteration counts).  The uncertainty is the support-restricted
-    one of ``unmix``: with the slack in the support the sum is free.
-
-    Returns dict(x, sx, rms, iters, lam, slack) like ``unmix``."""
-    if constraint == "sto":
-        return unmix(S, sigma, X, max_iter=max_iter)
-    if constraint not in ("slo", "pos"):
+    Returns dict(x, sx, rms, iters, lam) like ``unmix``, plus for slo the
+    slack w (= 1 - sum x) and its multiplier omega."""
+    if constraint not in CONSTRAINTS:
         raise ValueError("constraint must be sto, slo or pos")
-    M = POS_SCALE if constraint == "pos" else 1.0
-    S32 = _f32(S)
-    P, L = S32.shape
-    Sa = np.vstack([S32.astype(np.float64) * M, np.zeros((1, L))]).astype(np.float32)
-    r = unmix(Sa, sigma, X, max_iter=max_iter)
-    # support: lambda_i < x_i G_ii, with unit curvature for the slack (its
-    # spectrum is zero, G_ww = 0); the uncertainty on that support
-    G, _ = prep(Sa, sigma)
-    sx = np.empty_like(r["sx"])
-    for n in range(r["x"].shape[0]):
-        m = support(G, r["x"][n], r["lam"][n])
-        m[P] = r["lam"][n][P] < r["x"][n][P]
-        sx[n] = sigma_x(G, m)
-    out = dict(x=r["x"][:, :P] * M, sx=sx[:, :P] * M, rms=r["rms"],
-               iters=r["iters"].copy(), lam=r["lam"][:, :P], slack=r["x"][:, P] * M)
+    if constraint == "sto":
+        return unmix(S, sigma, X, max_iter=max_iter, nthreads=nthreads)
+    S, sigma, X = _f32(S), _f32(sigma), _f32(X)
+    P, L = S.shape
+    N = X.shape[0]
+    if X.shape[1] != L or sigma.shape[0] != L:
+        raise ValueError("shape mismatch between S, sigma and X")
+    out = dict(x=np.empty((N, P)), sx=np.empty((N, P)), rms=np.empty(N),
+               iters=np.empty(N, dtype=np.int32), lam=np.empty((N, P)),
+               slack=np.empty(N), omega=np.empty(N))
+    D, I = ctypes.c_double, ctypes.c_int
+    rc = _load().oracle_unmix_set(L, P, _p(S, ctypes.c_float), _p(sigma, ctypes.c_float),
+                                  N, _p(X, ctypes.c_float), CONSTRAINTS[constraint],
+                                  int(max_iter), int(nthreads), _p(out["x"], D),
+                                  _p(out["sx"], D), _p(out["rms"], D), _p(out["iters"], I),
+                                  _p(out["lam"], D), None, None, None, None,
+                                  _p(out["slack"], D), _p(out["omega"], D))
+    if rc:
+        raise ValueError(f"oracle_unmix_set: invalid input (code {rc})")
     if constraint == "pos":
-        bound = r["x"][:, P] <= 0.0
-        out["iters"][bound] = -np.abs(out["iters"][bound]) - 1
+        del out["slack"], out["omega"]
     return out
+
+
+def pos(G, c, s=0.0, max_iter=MAX_ITER):
+    """One pos problem min 1/2 x'Gx - c'x + s/2, x >= 0."""
+    G, c = _f64(G), _f64(c)
+    P = c.shape[0]
+    x = np.empty(P); lam = np.empty(P); it = ctypes.c_int(); mu = ctypes.c_double()
+    st = _load().oracle_pos(P, _p(G, ctypes.c_double), _p(c, ctypes.c_double), float(s),
+                            int(max_iter), _p(x, ctypes.c_double), _p(lam, ctypes.c_double),
+                            ctypes.byref(it), ctypes.byref(mu))
+    return dict(x=x, lam=lam, iters=it.value, mu=mu.value, status=st)
+
+
+def slo(G, c, s=0.0, max_iter=MAX_ITER):
+    """One slo problem min 1/2 x'Gx - c'x + s/2, x >= 0, 1'x <= 1."""
+    G, c = _f64(G), _f64(c)
+    P = c.shape[0]
+    x = np.empty(P); lam = np.empty(P); w = ctypes.c_double(); om = ctypes.c_double()
+    it = ctypes.c_int(); mu = ctypes.c_double()
+    st = _load().oracle_slo(P, _p(G, ctypes.c_double), _p(c, ctypes.c_double), float(s),
+                            int(max_iter), _p(x, ctypes.c_double), _p(lam, ctypes.c_double),
+                            ctypes.byref(w), ctypes.byref(om), ctypes.byref(it),
+                            ctypes.byref(mu))
+    return dict(x=x, lam=lam, w=w.value, omega=om.value, iters=it.value, mu=mu.value,
+                status=st)
+
+
+def sigma_x_set(G, in_S, bordered: bool):
+    G = _f64(G)
+    m = np.ascontiguousarray(in_S, dtype=np.int32)
+    P = m.shape[0]
+    sx = np.empty(P)
+    _load().oracle_sigma_x_set(P, _p(G, ctypes.c_double), _p(m, ctypes.c_int), int(bordered),
+                               _p(sx, ctypes.c_double))
+    return sx
 
 
 def unmix_cov(S, cov_inv, X, max_iter: int = MAX_ITER):

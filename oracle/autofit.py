@@ -1,4 +1,4 @@
-"""Auto-fit of the reference library (Sec. 2.5, "Estimation of
+"""Auto-fit of the reference library (Sec. 2.4, "Estimation of
 degeneracies"), plain numpy / scipy in fp64 (test infrastructure, like the
 rest of ``oracle``; the CUDA library shares no code with it).
 

@@ -4,12 +4,12 @@ CPU-baseline leg may use it; the CUDA library shares no code with it.
 
 * ``paper_extra_spectra``: the additional spectra of Sec. 2.5 and the
   Appendix table (names 33-44).
-* ``detect``: the detection conditions of Sec. 5 (introduction), evaluated
+* ``detect``: the detection conditions of Sec. 4 (introduction), evaluated
   pixel by pixel in float32 like the values they compare, with per-mineral
   counts, sums, arg-max and, given the truth, the positive / false
   detection counts of Sec. 3.1.
 * ``threshold_sums`` and ``thresholds``: eq. Threshold of Sec. 3.1.
-* ``second_pass``: the second unmixing of Sec. 6 with the detected spectra
+* ``second_pass``: the second unmixing of Sec. 5 with the detected spectra
   only, per pixel.
 """
 from __future__ import annotations
@@ -126,7 +126,7 @@ def thresholds(x, truth, n_minerals: int) -> np.ndarray:
 
 
 def second_pass(S, sigma, X, mask, n_minerals: int) -> dict:
-    """The second pass of Sec. 6: every pixel unmixed again with only the
+    """The second pass of Sec. 5: every pixel unmixed again with only the
     minerals detected in it (bits of ``mask`` below n_minerals) and all the
     additional spectra (columns >= n_minerals), with the sum-to-one oracle
     ``oracle.unmix``.  Abundances and uncertainties of the left-out

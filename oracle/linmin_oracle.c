@@ -39,6 +39,12 @@
  *     support S of the solution, and 0 off the support.
  *   RMS (Sec. 3.1, Sec. 4 detection conditions): sqrt(mean_l (y - S^T x)^2),
  *     unwhitened.
+ *   Constraint sets of the runs of Sec. 4 (Sec. 2.2): "slo" (x >= 0,
+ *     1^T x <= 1, the inequality with its own slack and multiplier) and
+ *     "pos" (x >= 0 alone), each an interior-point method of the same kind
+ *     written from its own KKT conditions (oracle_slo, oracle_pos); their
+ *     uncertainty is taken on the support, bordered by the sum constraint
+ *     only where it is active.
  */
 #include <math.h>
 #include <pthread.h>
@@ -269,6 +275,211 @@ int oracle_fcls(int P, const double *G, const double *c, double s, int max_iter,
     return status;
 }
 
+/* ------------------------------------- constraint sets pos and slo (Sec. 2.2)
+ *
+ * The paper unmixes real images under three constraint sets (Sec. 2.2 and
+ * the runs of Sec. 4): "sto" (x >= 0, 1^T x = 1, oracle_fcls above), "slo"
+ * (x >= 0, 1^T x <= 1) and "pos" (x >= 0 alone).  Each is written here from
+ * its own definition, as a primal-dual interior-point method of the same
+ * kind (Mehrotra predictor-corrector, separate primal and dual steps of
+ * 0.995 of the largest feasible one, LU with partial pivoting).
+ */
+
+/*
+ * pos: minimise 1/2 x'Gx - c'x + s/2 subject to x >= 0, with no bound on the
+ * sum.  KKT: G x - c - lambda = 0, x o lambda = 0, x, lambda >= 0.  Newton:
+ *    (G + X^-1 Lambda) dx = -r_d - X^-1 r_c,   dlambda = -X^-1 (r_c + Lambda dx)
+ * with r_d = G x - c - lambda, r_c = x o lambda - sigma mu 1, mu = x'lambda/P.
+ * Start x = 1/P, lambda = max(|c|_inf / P, 1e-3) 1.  Stop: |r_d|_inf <=
+ * 1e-12 (1 + |c|_inf) and mu <= 1e-13 (1 + |f|).  The minimiser is unique
+ * when G is regular (rank S = P).
+ */
+int oracle_pos(int P, const double *G, const double *c, double s, int max_iter,
+               double *x, double *lam, int *iters_out, double *mu_out)
+{
+    double *K = malloc(sizeof(double) * P * P);
+    int *piv = malloc(sizeof(int) * P);
+    double *rd = malloc(sizeof(double) * P), *rhs = malloc(sizeof(double) * P);
+    double *dxa = malloc(sizeof(double) * P), *dla = malloc(sizeof(double) * P);
+    double *dx = malloc(sizeof(double) * P), *dl = malloc(sizeof(double) * P);
+    double *rc = malloc(sizeof(double) * P);
+    int status = OR_MAXITER, it = 0;
+    double cinf = 0.0;
+    for (int i = 0; i < P; i++) cinf = fmax(cinf, fabs(c[i]));
+    const double lam0 = fmax(cinf / P, 1e-3);
+    for (int i = 0; i < P; i++) { x[i] = 1.0 / P; lam[i] = lam0; }
+    double mu = 0.0;
+    for (it = 0; it <= max_iter; it++) {
+        double rdinf = 0.0, xgx = 0.0, cx = 0.0;
+        mu = 0.0;
+        for (int i = 0; i < P; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < P; j++) acc += G[(size_t)i * P + j] * x[j];
+            rd[i] = acc - c[i] - lam[i];
+            rdinf = fmax(rdinf, fabs(rd[i]));
+            mu += x[i] * lam[i];
+            xgx += x[i] * acc;
+            cx += c[i] * x[i];
+        }
+        mu /= P;
+        const double f = 0.5 * xgx - cx + 0.5 * s;
+        if (rdinf <= 1e-12 * (1.0 + cinf) && mu <= 1e-13 * (1.0 + fabs(f))) {
+            status = OR_OK;
+            break;
+        }
+        if (it == max_iter) break;
+        for (int i = 0; i < P; i++) {
+            for (int j = 0; j < P; j++) K[(size_t)i * P + j] = G[(size_t)i * P + j];
+            K[(size_t)i * P + i] += lam[i] / x[i];
+        }
+        if (lu_factor(P, K, piv)) { status = OR_SINGULAR; break; }
+        /* predictor: r_c = x o lambda */
+        for (int i = 0; i < P; i++) rhs[i] = -rd[i] - lam[i];
+        lu_solve(P, K, piv, rhs);
+        for (int i = 0; i < P; i++) {
+            dxa[i] = rhs[i];
+            dla[i] = -lam[i] - lam[i] / x[i] * dxa[i];
+        }
+        double ap = max_step(P, x, dxa), ad = max_step(P, lam, dla);
+        double mua = 0.0;
+        for (int i = 0; i < P; i++) mua += (x[i] + ap * dxa[i]) * (lam[i] + ad * dla[i]);
+        mua /= P;
+        const double sig = pow(mua / mu, 3.0);
+        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu 1 */
+        for (int i = 0; i < P; i++) {
+            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
+            rhs[i] = -rd[i] - rc[i] / x[i];
+        }
+        lu_solve(P, K, piv, rhs);
+        for (int i = 0; i < P; i++) {
+            dx[i] = rhs[i];
+            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+        }
+        ap = fmin(1.0, 0.995 * max_step(P, x, dx));
+        ad = fmin(1.0, 0.995 * max_step(P, lam, dl));
+        for (int i = 0; i < P; i++) {
+            x[i] += ap * dx[i];
+            lam[i] += ad * dl[i];
+        }
+    }
+    for (int i = 0; i < P; i++) if (x[i] < 0.0) x[i] = 0.0;
+    *iters_out = it;
+    *mu_out = mu;
+    free(K); free(piv); free(rd); free(rhs); free(dxa); free(dla); free(dx); free(dl);
+    free(rc);
+    return status;
+}
+
+/*
+ * slo: minimise 1/2 x'Gx - c'x + s/2 subject to x >= 0 and 1'x <= 1.  The
+ * inequality gets its own slack w = 1 - 1'x >= 0 and multiplier omega >= 0.
+ * KKT: G x - c - lambda + omega 1 = 0, 1'x + w = 1, x o lambda = 0,
+ * w omega = 0.  Eliminating dlambda and dw from the Newton equations
+ * leaves the bordered system
+ *    [ G + X^-1 Lambda   1          ] [dx    ]   [ -r_d - X^-1 r_c      ]
+ *    [ 1^T              -w / omega  ] [domega] = [ -r_p + r_cw / omega  ]
+ * with r_d = G x - c - lambda + omega 1, r_p = 1'x + w - 1, r_c = x o lambda
+ * - sigma mu 1, r_cw = w omega - sigma mu, mu = (x'lambda + w omega)/(P+1);
+ * then dlambda = -X^-1 (r_c + Lambda dx), dw = -(r_cw + w domega) / omega.
+ * Start x = 1/(P+1) (so w = 1/(P+1)), lambda = omega = max(|c|_inf / P, 1e-3).
+ * Stop: |r_d|_inf <= 1e-12 (1 + |c|_inf), |r_p| <= 1e-14 and
+ * mu <= 1e-13 (1 + |f|).  The minimiser is unique when rank S = P.
+ */
+int oracle_slo(int P, const double *G, const double *c, double s, int max_iter,
+               double *x, double *lam, double *w_out, double *omega_out, int *iters_out,
+               double *mu_out)
+{
+    const int n = P + 1;
+    double *K = malloc(sizeof(double) * n * n);
+    int *piv = malloc(sizeof(int) * n);
+    double *rd = malloc(sizeof(double) * P), *rhs = malloc(sizeof(double) * n);
+    double *dxa = malloc(sizeof(double) * P), *dla = malloc(sizeof(double) * P);
+    double *dx = malloc(sizeof(double) * P), *dl = malloc(sizeof(double) * P);
+    double *rc = malloc(sizeof(double) * P);
+    int status = OR_MAXITER, it = 0;
+    double cinf = 0.0;
+    for (int i = 0; i < P; i++) cinf = fmax(cinf, fabs(c[i]));
+    const double lam0 = fmax(cinf / P, 1e-3);
+    for (int i = 0; i < P; i++) { x[i] = 1.0 / (P + 1); lam[i] = lam0; }
+    double w = 1.0 / (P + 1), om = lam0, mu = 0.0;
+    for (it = 0; it <= max_iter; it++) {
+        double rdinf = 0.0, rp = w - 1.0, xgx = 0.0, cx = 0.0;
+        mu = w * om;
+        for (int i = 0; i < P; i++) {
+            double acc = 0.0;
+            for (int j = 0; j < P; j++) acc += G[(size_t)i * P + j] * x[j];
+            rd[i] = acc - c[i] - lam[i] + om;
+            rdinf = fmax(rdinf, fabs(rd[i]));
+            rp += x[i];
+            mu += x[i] * lam[i];
+            xgx += x[i] * acc;
+            cx += c[i] * x[i];
+        }
+        mu /= P + 1;
+        const double f = 0.5 * xgx - cx + 0.5 * s;
+        if (rdinf <= 1e-12 * (1.0 + cinf) && fabs(rp) <= 1e-14 &&
+            mu <= 1e-13 * (1.0 + fabs(f))) {
+            status = OR_OK;
+            break;
+        }
+        if (it == max_iter) break;
+        for (int i = 0; i < P; i++) {
+            for (int j = 0; j < P; j++) K[(size_t)i * n + j] = G[(size_t)i * P + j];
+            K[(size_t)i * n + i] += lam[i] / x[i];
+            K[(size_t)i * n + P] = 1.0;
+            K[(size_t)P * n + i] = 1.0;
+        }
+        K[(size_t)P * n + P] = -w / om;
+        if (lu_factor(n, K, piv)) { status = OR_SINGULAR; break; }
+        /* predictor: r_c = x o lambda, r_cw = w omega */
+        for (int i = 0; i < P; i++) rhs[i] = -rd[i] - lam[i];
+        rhs[P] = -rp + w;
+        lu_solve(n, K, piv, rhs);
+        for (int i = 0; i < P; i++) {
+            dxa[i] = rhs[i];
+            dla[i] = -lam[i] - lam[i] / x[i] * dxa[i];
+        }
+        const double doa = rhs[P];
+        const double dwa = -w - w * doa / om;
+        double ap = fmin(max_step(P, x, dxa), max_step(1, &w, &dwa));
+        double ad = fmin(max_step(P, lam, dla), max_step(1, &om, &doa));
+        double mua = (w + ap * dwa) * (om + ad * doa);
+        for (int i = 0; i < P; i++) mua += (x[i] + ap * dxa[i]) * (lam[i] + ad * dla[i]);
+        mua /= P + 1;
+        const double sig = pow(mua / mu, 3.0);
+        /* corrector */
+        for (int i = 0; i < P; i++) {
+            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
+            rhs[i] = -rd[i] - rc[i] / x[i];
+        }
+        const double rcw = w * om + dwa * doa - sig * mu;
+        rhs[P] = -rp + rcw / om;
+        lu_solve(n, K, piv, rhs);
+        for (int i = 0; i < P; i++) {
+            dx[i] = rhs[i];
+            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+        }
+        const double dom = rhs[P];
+        const double dw = -(rcw + w * dom) / om;
+        ap = fmin(1.0, 0.995 * fmin(max_step(P, x, dx), max_step(1, &w, &dw)));
+        ad = fmin(1.0, 0.995 * fmin(max_step(P, lam, dl), max_step(1, &om, &dom)));
+        for (int i = 0; i < P; i++) {
+            x[i] += ap * dx[i];
+            lam[i] += ad * dl[i];
+        }
+        w += ap * dw;
+        om += ad * dom;
+    }
+    for (int i = 0; i < P; i++) if (x[i] < 0.0) x[i] = 0.0;
+    *w_out = w;
+    *omega_out = om;
+    *iters_out = it;
+    *mu_out = mu;
+    free(K); free(piv); free(rd); free(rhs); free(dxa); free(dla); free(dx); free(dl);
+    free(rc);
+    return status;
+}
+
 /* --------------------------------------------------------- uncertainty */
 
 /* Support of the final iterate: i is active when its barrier term
@@ -284,25 +495,30 @@ int oracle_support(int P, const double *G, const double *x, const double *lam,
     return k;
 }
 
-/* sigma_x: sqrt of the diagonal of the top-left block of
- * [[G_SS, 1],[1^T, 0]]^-1 on the support S, 0 elsewhere.  Returns 0, or 1
- * when the bordered system on S is singular (sx is then set to NaN on S). */
-int oracle_sigma_x(int P, const double *G, const int *in_S, double *sx)
+/* sigma_x of an active set: sqrt of the diagonal of the inverse of the
+ * Hessian restricted to the support S, bordered by the sum constraint when
+ * it is active (bordered != 0: top-left block of [[G_SS, 1],[1^T, 0]]^-1;
+ * else (G_SS)^-1), and 0 off the support.  Returns 0, or 1 when that system
+ * is singular (sx is then set to NaN on S). */
+int oracle_sigma_x_set(int P, const double *G, const int *in_S, int bordered, double *sx)
 {
     int k = 0;
     int *idx = malloc(sizeof(int) * P);
     for (int i = 0; i < P; i++) if (in_S[i]) idx[k++] = i;
     for (int i = 0; i < P; i++) sx[i] = 0.0;
-    int n = k + 1, bad = 0;
-    double *K = malloc(sizeof(double) * n * n);
-    int *piv = malloc(sizeof(int) * n);
-    double *e = malloc(sizeof(double) * n);
+    const int n = k + (bordered ? 1 : 0);
+    int bad = 0;
+    double *K = malloc(sizeof(double) * (n * n + 1));
+    int *piv = malloc(sizeof(int) * (n + 1));
+    double *e = malloc(sizeof(double) * (n + 1));
     for (int a = 0; a < k; a++) {
         for (int b = 0; b < k; b++) K[(size_t)a * n + b] = G[(size_t)idx[a] * P + idx[b]];
-        K[(size_t)a * n + k] = 1.0;
-        K[(size_t)k * n + a] = 1.0;
+        if (bordered) {
+            K[(size_t)a * n + k] = 1.0;
+            K[(size_t)k * n + a] = 1.0;
+        }
     }
-    K[(size_t)k * n + k] = 0.0;
+    if (bordered) K[(size_t)k * n + k] = 0.0;
     if (k == 0 || lu_factor(n, K, piv)) {
         bad = 1;
         for (int a = 0; a < k; a++) sx[idx[a]] = NAN;
@@ -316,6 +532,12 @@ int oracle_sigma_x(int P, const double *G, const int *in_S, double *sx)
     }
     free(idx); free(K); free(piv); free(e);
     return bad;
+}
+
+/* sigma_x under the sum-to-one constraint (always bordered). */
+int oracle_sigma_x(int P, const double *G, const int *in_S, double *sx)
+{
+    return oracle_sigma_x_set(P, G, in_S, 1, sx);
 }
 
 /* Unwhitened RMS of the fit: sqrt(mean_l (y_l - sum_j x_j S_jl)^2). */
@@ -340,6 +562,8 @@ typedef struct {
     long long lo, hi;
     double *x, *sx, *rms, *lam, *nu, *mu;
     int *iters, *status, *ksup;
+    int constraint;               /* 0 sto, 1 slo, 2 pos */
+    double *slack, *omega;        /* slo: w and omega per pixel (optional) */
 } job_t;
 
 static void *unmix_range(void *arg)
@@ -355,9 +579,26 @@ static void *unmix_range(void *arg)
         int it;
         double *x = j->x + (size_t)n * P;
         oracle_project(L, P, j->B, j->sigma, y, c, &s);
-        int st = oracle_fcls(P, j->G, c, s, j->max_iter, x, lam, &nu, &it, &mu);
-        int k = oracle_support(P, j->G, x, lam, in_S);
-        if (oracle_sigma_x(P, j->G, in_S, j->sx + (size_t)n * P)) st |= 4;
+        int st, k, bordered = 1;
+        double w = 0.0, om = 0.0;
+        if (j->constraint == 2) {
+            st = oracle_pos(P, j->G, c, s, j->max_iter, x, lam, &it, &mu);
+            nu = 0.0;
+            bordered = 0;
+        } else if (j->constraint == 1) {
+            st = oracle_slo(P, j->G, c, s, j->max_iter, x, lam, &w, &om, &it, &mu);
+            nu = om;
+            /* the sum constraint is active when its multiplier exceeds its
+             * slack (unit curvature for the slack, as lambda_i < x_i G_ii
+             * for the coordinates) */
+            bordered = om > w;
+        } else {
+            st = oracle_fcls(P, j->G, c, s, j->max_iter, x, lam, &nu, &it, &mu);
+        }
+        k = oracle_support(P, j->G, x, lam, in_S);
+        if (oracle_sigma_x_set(P, j->G, in_S, bordered, j->sx + (size_t)n * P)) st |= 4;
+        if (j->slack) j->slack[n] = w;
+        if (j->omega) j->omega[n] = om;
         j->rms[n] = oracle_rms(L, P, j->S, x, y);
         j->iters[n] = (st & 3) == OR_OK ? it : -it - 1;
         if (j->status) j->status[n] = st;
@@ -383,11 +624,12 @@ int oracle_nproc(void)
  * status, ksup (N).  nthreads <= 0 uses every online core.  Returns 0, or a
  * non-zero code for invalid arguments.
  */
-int oracle_unmix(int L, int P, const float *S, const float *sigma, long long N,
-                 const float *X, int max_iter, int nthreads, double *x,
-                 double *sx, double *rms, int *iters, double *lam, double *nu,
-                 double *mu, int *status, int *ksup)
+int oracle_unmix_set(int L, int P, const float *S, const float *sigma, long long N,
+                     const float *X, int constraint, int max_iter, int nthreads, double *x,
+                     double *sx, double *rms, int *iters, double *lam, double *nu,
+                     double *mu, int *status, int *ksup, double *slack, double *omega)
 {
+    if (constraint < 0 || constraint > 2) return 1;
     if (N < 0 || L <= 0 || P <= 0) return 1;
     if (N == 0) return 0;
     double *G = malloc(sizeof(double) * P * P);
@@ -401,11 +643,22 @@ int oracle_unmix(int L, int P, const float *S, const float *sigma, long long N,
     for (int t = 0; t < nthreads; t++) {
         job_t j = {L, P, max_iter, S, sigma, X, G, B,
                    N * t / nthreads, N * (t + 1) / nthreads,
-                   x, sx, rms, lam, nu, mu, iters, status, ksup};
+                   x, sx, rms, lam, nu, mu, iters, status, ksup,
+                   constraint, slack, omega};
         jobs[t] = j;
         pthread_create(&th[t], NULL, unmix_range, &jobs[t]);
     }
     for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     free(th); free(jobs); free(G); free(B);
     return 0;
+}
+
+/* Sum-to-one unmixing of a whole cube (the sto constraint set). */
+int oracle_unmix(int L, int P, const float *S, const float *sigma, long long N,
+                 const float *X, int max_iter, int nthreads, double *x,
+                 double *sx, double *rms, int *iters, double *lam, double *nu,
+                 double *mu, int *status, int *ksup)
+{
+    return oracle_unmix_set(L, P, S, sigma, N, X, 0, max_iter, nthreads, x, sx, rms, iters,
+                            lam, nu, mu, status, ksup, NULL, NULL);
 }

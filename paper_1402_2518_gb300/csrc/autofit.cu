@@ -1,4 +1,4 @@
-// Auto-fit of the reference library (Sec. 2.5, "Estimation of
+// Auto-fit of the reference library (Sec. 2.4, "Estimation of
 // degeneracies"): every spectrum S_n is fitted by the P - 1 others,
 // S_n = A'.S' + E, once without constraints and once with A' >= 0.
 //

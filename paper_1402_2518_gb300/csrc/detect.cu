@@ -1,5 +1,5 @@
 // Detection products: the paper's additional spectra (Sec. 2.5, Appendix),
-// the per-pixel detection conditions (Sec. 5), and the statistics of the
+// the per-pixel detection conditions (Sec. 4, introduction), and the statistics of the
 // per-mineral threshold (Sec. 3.1, eq. Threshold).
 //
 // Both device kernels stream the N x P abundance array once with the lane

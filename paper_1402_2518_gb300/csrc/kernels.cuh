@@ -74,7 +74,7 @@ cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
                                const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st);
 // slo / pos outputs from the slack-augmented internal problem
-// Per-pixel column subsets (the second pass of Sec. 6): for pixel n and
+// Per-pixel column subsets (the second pass of Sec. 5): for pixel n and
 // each column j < n_minerals whose bit is clear in mask[n], c~_j -= K_n
 // with K_n = 2 (max_k |c~_k| + P + rho) + 1, an exact linear penalty: the
 // multiplier of x_j = 0 in the problem without column j is bounded by

@@ -1,4 +1,4 @@
-// Second pass (Sec. 6): once the detection step has run, every pixel is
+// Second pass (Sec. 5): once the detection step has run, every pixel is
 // unmixed again with only the minerals detected in it and the additional
 // spectra, which sharpens the abundances of the minerals that are there.
 //

@@ -1,4 +1,4 @@
-"""Library auto-fit (Sec. 2.5) on the device through the C ABI against the
+"""Library auto-fit (Sec. 2.4) on the device through the C ABI against the
 oracle (oracle.autofit): residues of the unconstrained and the
 non-negative fits of every spectrum by the others (unique), their RMS, and
 the non-negative coefficients (equal where the others are independent,
@@ -81,7 +81,7 @@ def test_autofit_matches_oracle(pkg, name):
 
 
 def test_autofit_degeneracy_claim(pkg):
-    """The point of Sec. 2.5: without constraints the dependent level/slope
+    """The point of Sec. 2.4: without constraints the dependent level/slope
     spectra are fitted exactly by the others, under x >= 0 the slopes are
     not; and the unconstrained residue never exceeds the constrained one."""
     got = run(pkg, LIBS["omega_P36"])

@@ -1,5 +1,6 @@
 """The slo (sum x <= 1) and pos (x >= 0) constraint sets on the device
-against the oracle (oracle.unmix_constraint), with the same bars as the
+against the oracle (oracle.unmix_constraint: interior-point methods written
+from each set's own definition), with the same bars as the
 sum-to-one path: x 1e-4, uncertainties 1e-4 on unambiguous pixels, RMS 1e-4
 relative.  Libraries have rank S = P (minerals, or the OMEGA-shaped library
 without its decreasing slope)."""
@@ -41,15 +42,13 @@ def omega_rank_full(n_pix):
     return S, cube.sigma, cube.X
 
 
-def check(got, ref, S, sigma, M=1.0):
-    """M: the scale of the oracle's internal problem (its lambda refers to
-    x / M and the Gram M^2 G)."""
+def check(got, ref, S, sigma):
     x, sx, rms, it = got
     assert np.all(it > 0) and np.all(x >= 0)
     assert np.abs(x - ref["x"]).max() <= 1e-4
     w2 = 1.0 / sigma.astype(np.float64) ** 2
     gd = (S.astype(np.float64) ** 2 * w2).sum(1)
-    ratio = ref["lam"] / np.maximum(ref["x"], 1e-300) / gd[None, :] / M
+    ratio = ref["lam"] / np.maximum(ref["x"], 1e-300) / gd[None, :]
     ok = ~np.any((ratio > 1e-3) & (ratio < 1e3), axis=1)
     assert ok.mean() > 0.7
     assert np.abs(sx[ok] - ref["sx"][ok]).max() <= 1e-4 * max(1.0, np.abs(ref["sx"][ok]).max())
@@ -63,7 +62,7 @@ def test_random_full_rank(pkg, constraint):
     ref = oracle.unmix_constraint(cube.S, cube.sigma, X, constraint)
     st, nbad, got = run(pkg, cube.S, cube.sigma, X, constraint)
     assert st == 0 and nbad == 0
-    check(got, ref, cube.S, cube.sigma, oracle.POS_SCALE if constraint == "pos" else 1.0)
+    check(got, ref, cube.S, cube.sigma)
     if constraint == "slo":
         assert np.all(got[0].sum(1) <= 1 + 1e-5)
         tot = ref["x"].sum(1)
@@ -76,7 +75,7 @@ def test_omega_shaped(pkg, constraint):
     ref = oracle.unmix_constraint(S, sigma, X, constraint)
     st, nbad, got = run(pkg, S, sigma, X, constraint)
     assert st == 0 and nbad == 0
-    check(got, ref, S, sigma, oracle.POS_SCALE if constraint == "pos" else 1.0)
+    check(got, ref, S, sigma)
 
 
 def test_rank_and_size_refusals(pkg):
@@ -94,3 +93,24 @@ def test_rank_and_size_refusals(pkg):
     with pytest.raises(linmin.LinminError) as e:
         pkg.linmin_create(big.S, big.L, big.P, opt)
     assert e.value.status == linmin.LINMIN_ERR_UNSUPPORTED
+
+
+def test_pos_sum_bound_is_flagged(pkg):
+    """The device solves pos as slo on M S with M = LINMIN_POS_SCALE, which is
+    exact while sum x < M.  A pixel whose pos minimiser has a larger sum is
+    reported, not silently clipped: negative iteration count and
+    LINMIN_ERR_NOT_CONVERGED; every other pixel still matches the oracle."""
+    from paper_1402_2518_gb300 import linmin
+    cube = synth.random_instance(3302, 200, 96, 12, n_extras=0)
+    X = cube.X.astype(np.float64).copy()
+    big = np.arange(0, cube.N, 10)
+    X[big] = X[big] * (2.0 * linmin.LINMIN_POS_SCALE)          # sums near 2 M
+    X = X.astype(np.float32)
+    ref = oracle.unmix_constraint(cube.S, cube.sigma, X, "pos")
+    over = ref["x"].sum(1) >= linmin.LINMIN_POS_SCALE
+    assert over[big].all() and not over[np.setdiff1d(np.arange(cube.N), big)].any()
+    st, nbad, got = run(pkg, cube.S, cube.sigma, X, "pos")
+    x, sx, rms, it = got
+    assert st == linmin.LINMIN_ERR_NOT_CONVERGED and nbad == over.sum()
+    assert np.all(it[over] < 0) and np.all(it[~over] > 0)
+    assert np.abs(x[~over] - ref["x"][~over]).max() <= 1e-4

@@ -1,4 +1,4 @@
-"""Second pass of Sec. 6 on the device through the C ABI against the
+"""Second pass of Sec. 5 on the device through the C ABI against the
 oracle (oracle.detection.second_pass), on the same masks: the oracle's own
 detections on the surface mixtures of Sec. 3.1, the true minerals, and
 random masks over many groups with a ragged pixel count."""
@@ -86,7 +86,7 @@ def test_second_pass_on_detections(pkg):
 
 def test_second_pass_true_minerals_sharpen(pkg):
     """With the minerals that are really there, the second pass brings the
-    abundances closer to the truth than the first (the claim of Sec. 6)."""
+    abundances closer to the truth than the first (the claim of Sec. 5)."""
     cube, truth = synth.surface_mixtures()
     nm = 32
     st, got = run(pkg, cube.S, cube.X, cube.sigma, truth, nm)

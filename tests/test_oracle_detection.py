@@ -1,9 +1,9 @@
 """Pins of the detection-products oracle (oracle.detection) against
 hand-worked cases: the additional spectra of the Appendix table at u = 0,
 1/2, 1; the rank deficiency those spectra bring under sum-to-one; the three
-detection conditions of Sec. 5 on a five-pixel case; eq. Threshold of
+detection conditions of Sec. 4 on a five-pixel case; eq. Threshold of
 Sec. 3.1 on a four-pixel case; the surface-mixture recipe of Sec. 3.1; and
-the library auto-fit of Sec. 2.5 (oracle.autofit) against exact
+the library auto-fit of Sec. 2.4 (oracle.autofit) against exact
 dependencies, brute-force NNLS and the least-squares normal equations."""
 import math
 

@@ -398,9 +398,58 @@ def test_pos_kkt_and_uncertainty():
         if (~S_).any():
             assert g[~S_].min() >= -1e-6 * scale
         idx = np.flatnonzero(S_)
-        ratio = r["lam"][n] / np.maximum(x / oracle.POS_SCALE, 1e-300) / (np.diag(G) * oracle.POS_SCALE ** 2)
+        ratio = r["lam"][n] / np.maximum(x, 1e-300) / np.diag(G)
         if np.any((ratio > 1e-3) & (ratio < 1e3)):
             continue                                 # no strict complementarity
         sx = np.sqrt(np.diag(np.linalg.inv(G[np.ix_(idx, idx)])))
         np.testing.assert_allclose(r["sx"][n][idx], sx, rtol=1e-6)
         assert np.all(r["sx"][n][~S_] == 0.0)
+
+
+def test_pos_brute_force_supports():
+    """Tiny problems: the pos minimiser is the best feasible unconstrained
+    least-squares solution over all supports (no sum constraint at all,
+    so sums well above 1 occur)."""
+    import itertools
+    cube = _full_rank_instance(65, 12, 30, 5)
+    X = (cube.X.astype(np.float64) * np.linspace(0.5, 3.0, cube.N)[:, None]).astype(np.float32)
+    r = oracle.unmix_constraint(cube.S, cube.sigma, X, "pos")
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    P = cube.P
+    assert r["x"].sum(1).max() > 2.0
+    for n in range(cube.N):
+        c = B @ X[n].astype(np.float64)
+        best, xb = 0.0, np.zeros(P)            # the empty support: x = 0, f = 0
+        for k in range(1, P + 1):
+            for S_ in itertools.combinations(range(P), k):
+                idx = list(S_)
+                xs = np.linalg.solve(G[np.ix_(idx, idx)], c[idx])
+                if xs.min() < -1e-12:
+                    continue
+                x = np.zeros(P); x[idx] = xs
+                f = 0.5 * x @ G @ x - c @ x
+                if f < best:
+                    best, xb = f, x
+        assert np.abs(r["x"][n] - xb).max() <= 1e-7 * max(1.0, xb.max())
+
+
+def test_slo_kkt_certificate():
+    """slo: gradient + omega vanishes on the support and is >= 0 off it;
+    omega >= 0, slack w = 1 - sum x >= 0 and w omega ~ 0 (one of the two is
+    negligible on every pixel)."""
+    cube = _full_rank_instance(66, 60, 50, 8)
+    X = (cube.X.astype(np.float64) * np.linspace(0.6, 1.5, cube.N)[:, None]).astype(np.float32)
+    r = oracle.unmix_constraint(cube.S, cube.sigma, X, "slo")
+    assert np.all(r["iters"] > 0)
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    scale = np.max(np.diag(G))
+    np.testing.assert_allclose(r["slack"], 1.0 - r["x"].sum(1), atol=1e-12)
+    assert np.all(r["slack"] >= -1e-14) and np.all(r["omega"] >= 0.0)
+    assert np.all(np.minimum(r["slack"], r["omega"] / scale) <= 1e-9)
+    for n in range(cube.N):
+        x = r["x"][n]
+        g = G @ x - B @ X[n].astype(np.float64) + r["omega"][n]
+        S_ = x > 1e-9
+        assert np.abs(g[S_]).max() <= 1e-6 * scale
+        if (~S_).any():
+            assert g[~S_].min() >= -1e-6 * scale
