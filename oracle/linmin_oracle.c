@@ -169,8 +169,13 @@ static double max_step(int P, const double *v, const double *dv)
  * Start: x = 1/P, lambda = max(|c|_inf / P, 1e-3) 1, nu = 0.
  * Stop:  |r_d|_inf <= 1e-12 (1 + |c|_inf), |r_p| <= 1e-14,
  *        mu <= 1e-13 (1 + |f|), or max_iter iterations.
- * Step:  alpha_p, alpha_d = min(1, 0.995 * max feasible), primal and dual
- *        separately.
+ * Step:  Mehrotra's corrected direction, or a centred Newton direction
+ *        (r_c = x o lambda - mu/2) when the corrected step would not reduce
+ *        mu by 1% of its length; one length alpha = min(1, 0.995 * max
+ *        feasible) for x, lambda and nu together.  In a QP the dual residual r_d = G x - c - lambda +
+ *        nu 1 couples x and (lambda, nu): after a step it is r_d (1 -
+ *        alpha_d) + (alpha_p - alpha_d) G dx, so separate primal and dual
+ *        lengths (the linear-programming rule) can leave it stuck.
  */
 int oracle_fcls(int P, const double *G, const double *c, double s, int max_iter,
                 double *x, double *lam, double *nu_out, int *iters_out,
@@ -241,25 +246,34 @@ int oracle_fcls(int P, const double *G, const double *c, double s, int max_iter,
         mua /= P;
         double sig = pow(mua / mu, 3.0);
 
-        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu */
-        for (int i = 0; i < P; i++) {
-            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
-            rhs[i] = -rd[i] - rc[i] / x[i];
+        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu; if
+         * its step does not reduce mu by at least 1% of the step length,
+         * a centred Newton step (r_c = x o lambda - mu/2) instead, which
+         * breaks the cycles the corrector can fall into */
+        double dnu = 0.0, a = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int i = 0; i < P; i++) {
+                rc[i] = pass == 0 ? x[i] * lam[i] + dxa[i] * dla[i] - sig * mu
+                                  : x[i] * lam[i] - 0.5 * mu;
+                rhs[i] = -rd[i] - rc[i] / x[i];
+            }
+            rhs[P] = -rp;
+            lu_solve(n, K, piv, rhs);
+            dnu = rhs[P];
+            for (int i = 0; i < P; i++) {
+                dx[i] = rhs[i];
+                dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+            }
+            a = fmin(1.0, 0.995 * fmin(max_step(P, x, dx), max_step(P, lam, dl)));
+            double mun = 0.0;
+            for (int i = 0; i < P; i++) mun += (x[i] + a * dx[i]) * (lam[i] + a * dl[i]);
+            if (mun / P <= (1.0 - 0.01 * a) * mu) break;
         }
-        rhs[P] = -rp;
-        lu_solve(n, K, piv, rhs);
-        double dnu = rhs[P];
         for (int i = 0; i < P; i++) {
-            dx[i] = rhs[i];
-            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+            x[i] += a * dx[i];
+            lam[i] += a * dl[i];
         }
-        ap = fmin(1.0, 0.995 * max_step(P, x, dx));
-        ad = fmin(1.0, 0.995 * max_step(P, lam, dl));
-        for (int i = 0; i < P; i++) {
-            x[i] += ap * dx[i];
-            lam[i] += ad * dl[i];
-        }
-        nu += ad * dnu;
+        nu += a * dnu;
         (void)tmp;
     }
     /* x <- max(x, 0) / sum */
@@ -281,8 +295,9 @@ int oracle_fcls(int P, const double *G, const double *c, double s, int max_iter,
  * the runs of Sec. 4): "sto" (x >= 0, 1^T x = 1, oracle_fcls above), "slo"
  * (x >= 0, 1^T x <= 1) and "pos" (x >= 0 alone).  Each is written here from
  * its own definition, as a primal-dual interior-point method of the same
- * kind (Mehrotra predictor-corrector, separate primal and dual steps of
- * 0.995 of the largest feasible one, LU with partial pivoting).
+ * kind (Mehrotra predictor-corrector, one step length of 0.995 of the
+ * largest feasible one for primal and dual together, LU with partial
+ * pivoting).
  */
 
 /*
@@ -345,21 +360,29 @@ int oracle_pos(int P, const double *G, const double *c, double s, int max_iter,
         for (int i = 0; i < P; i++) mua += (x[i] + ap * dxa[i]) * (lam[i] + ad * dla[i]);
         mua /= P;
         const double sig = pow(mua / mu, 3.0);
-        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu 1 */
-        for (int i = 0; i < P; i++) {
-            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
-            rhs[i] = -rd[i] - rc[i] / x[i];
+        /* corrector: r_c = x o lambda + dx_aff o dlam_aff - sigma mu 1, or
+         * the centred Newton step when it does not reduce mu (as in
+         * oracle_fcls) */
+        double a = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int i = 0; i < P; i++) {
+                rc[i] = pass == 0 ? x[i] * lam[i] + dxa[i] * dla[i] - sig * mu
+                                  : x[i] * lam[i] - 0.5 * mu;
+                rhs[i] = -rd[i] - rc[i] / x[i];
+            }
+            lu_solve(P, K, piv, rhs);
+            for (int i = 0; i < P; i++) {
+                dx[i] = rhs[i];
+                dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+            }
+            a = fmin(1.0, 0.995 * fmin(max_step(P, x, dx), max_step(P, lam, dl)));
+            double mun = 0.0;
+            for (int i = 0; i < P; i++) mun += (x[i] + a * dx[i]) * (lam[i] + a * dl[i]);
+            if (mun / P <= (1.0 - 0.01 * a) * mu) break;
         }
-        lu_solve(P, K, piv, rhs);
         for (int i = 0; i < P; i++) {
-            dx[i] = rhs[i];
-            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
-        }
-        ap = fmin(1.0, 0.995 * max_step(P, x, dx));
-        ad = fmin(1.0, 0.995 * max_step(P, lam, dl));
-        for (int i = 0; i < P; i++) {
-            x[i] += ap * dx[i];
-            lam[i] += ad * dl[i];
+            x[i] += a * dx[i];
+            lam[i] += a * dl[i];
         }
     }
     for (int i = 0; i < P; i++) if (x[i] < 0.0) x[i] = 0.0;
@@ -447,28 +470,36 @@ int oracle_slo(int P, const double *G, const double *c, double s, int max_iter,
         for (int i = 0; i < P; i++) mua += (x[i] + ap * dxa[i]) * (lam[i] + ad * dla[i]);
         mua /= P + 1;
         const double sig = pow(mua / mu, 3.0);
-        /* corrector */
-        for (int i = 0; i < P; i++) {
-            rc[i] = x[i] * lam[i] + dxa[i] * dla[i] - sig * mu;
-            rhs[i] = -rd[i] - rc[i] / x[i];
+        /* corrector, or the centred Newton step when it does not reduce
+         * mu (as in oracle_fcls) */
+        double dom = 0.0, dw = 0.0, a = 0.0;
+        for (int pass = 0; pass < 2; pass++) {
+            for (int i = 0; i < P; i++) {
+                rc[i] = pass == 0 ? x[i] * lam[i] + dxa[i] * dla[i] - sig * mu
+                                  : x[i] * lam[i] - 0.5 * mu;
+                rhs[i] = -rd[i] - rc[i] / x[i];
+            }
+            const double rcw = pass == 0 ? w * om + dwa * doa - sig * mu : w * om - 0.5 * mu;
+            rhs[P] = -rp + rcw / om;
+            lu_solve(n, K, piv, rhs);
+            for (int i = 0; i < P; i++) {
+                dx[i] = rhs[i];
+                dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+            }
+            dom = rhs[P];
+            dw = -(rcw + w * dom) / om;
+            a = fmin(1.0, 0.995 * fmin(fmin(max_step(P, x, dx), max_step(1, &w, &dw)),
+                                       fmin(max_step(P, lam, dl), max_step(1, &om, &dom))));
+            double mun = (w + a * dw) * (om + a * dom);
+            for (int i = 0; i < P; i++) mun += (x[i] + a * dx[i]) * (lam[i] + a * dl[i]);
+            if (mun / (P + 1) <= (1.0 - 0.01 * a) * mu) break;
         }
-        const double rcw = w * om + dwa * doa - sig * mu;
-        rhs[P] = -rp + rcw / om;
-        lu_solve(n, K, piv, rhs);
         for (int i = 0; i < P; i++) {
-            dx[i] = rhs[i];
-            dl[i] = (-rc[i] - lam[i] * dx[i]) / x[i];
+            x[i] += a * dx[i];
+            lam[i] += a * dl[i];
         }
-        const double dom = rhs[P];
-        const double dw = -(rcw + w * dom) / om;
-        ap = fmin(1.0, 0.995 * fmin(max_step(P, x, dx), max_step(1, &w, &dw)));
-        ad = fmin(1.0, 0.995 * fmin(max_step(P, lam, dl), max_step(1, &om, &dom)));
-        for (int i = 0; i < P; i++) {
-            x[i] += ap * dx[i];
-            lam[i] += ad * dl[i];
-        }
-        w += ap * dw;
-        om += ad * dom;
+        w += a * dw;
+        om += a * dom;
     }
     for (int i = 0; i < P; i++) if (x[i] < 0.0) x[i] = 0.0;
     *w_out = w;

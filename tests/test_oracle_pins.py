@@ -453,3 +453,29 @@ def test_slo_kkt_certificate():
         assert np.abs(g[S_]).max() <= 1e-6 * scale
         if (~S_).any():
             assert g[~S_].min() >= -1e-6 * scale
+
+
+# Pixels of the seeded full-size workloads on which the interior point, with
+# separate primal and dual step lengths and no centring fallback, stalled
+# (the dual residual stuck, or a two-iteration cycle between near-dependent
+# spectra with mu bouncing between two values).
+HARD_PIXELS = {"omega_262k_L184_P36": [107698, 118302, 126310, 135370, 161210, 211715,
+                                       218946, 260039],
+               "crism_307k_L240_P48": [204239]}
+
+
+@pytest.mark.parametrize("name", sorted(HARD_PIXELS))
+def test_converges_on_pixels_that_stalled(name):
+    """Every solve converges (stop test met, not the cap) and its result is
+    the minimiser: the Frank-Wolfe gap (an upper bound on f(x) - f*) is at
+    the rounding level of the problem."""
+    spec = [w for w in synth.WORKLOADS if w.name == name][0]
+    idx = HARD_PIXELS[name]
+    cube = synth.make_cube(spec, n_pix=max(idx) + 1)
+    r = oracle.unmix(cube.S, cube.sigma, cube.X[idx])
+    assert np.all(r["iters"] > 0) and np.all(r["status"] == 0)
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    scale = np.trace(G) / G.shape[0]
+    for k, n in enumerate(idx):
+        c = B @ cube.X[n].astype(np.float64)
+        assert _pins.fw_gap(G, c, r["x"][k]) <= 1e-9 * scale
