@@ -255,6 +255,16 @@ LINMIN_API linmin_status linmin_autotune(linmin_handle h, const float *cube, lon
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);
 
+/* Measured FP32 throughput of the current device, the roofline peak of the
+ * interior-point solve (which is bound by FP32 FMAs): TFLOP/s (2 flops
+ * per FMA) of independent FMA chains on every SM, as scalar FFMA
+ * (*tflops_ffma) and packed two-wide FFMA2 (*tflops_ffma2), each timed with
+ * CUDA events on cuda_stream (NULL: the default stream) around a second
+ * launch of fixed work (~2 ms).  Synchronous; uses a small stream-ordered
+ * allocation.  The paper has no counterpart: a measurement utility. */
+LINMIN_API linmin_status linmin_fp32_peak(double *tflops_ffma, double *tflops_ffma2,
+                                          void *cuda_stream);
+
 /* ------------------------------------------------------------------ */
 /*
  * Serving: continuous batching of unmixing requests.  The paper has no

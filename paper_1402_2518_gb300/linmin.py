@@ -41,7 +41,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
             "linmin_thresholds", "linmin_autofit", "linmin_second_pass",
-            "linmin_unmix_masked", "linmin_noalloc_scratch_bytes")
+            "linmin_unmix_masked", "linmin_noalloc_scratch_bytes", "linmin_fp32_peak")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -133,6 +133,9 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
                                                  ctypes.POINTER(ctypes.c_ulonglong)]
     lib.linmin_noalloc_scratch_bytes.restype = ctypes.c_int
+    lib.linmin_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.linmin_fp32_peak.restype = ctypes.c_int
     SV = ctypes.c_void_p
     lib.linmin_server_default_options.argtypes = [ctypes.POINTER(linmin_server_options)]
     lib.linmin_server_default_options.restype = ctypes.c_int
@@ -307,6 +310,13 @@ def linmin_noalloc_scratch_bytes(L: int, P: int, N: int) -> tuple[int, int]:
     b = ctypes.c_ulonglong(0)
     st = lib().linmin_noalloc_scratch_bytes(int(L), int(P), int(N), ctypes.byref(b))
     return st, int(b.value)
+
+
+def linmin_fp32_peak(stream=None) -> tuple[float, float]:
+    """Measured (FFMA, FFMA2) TFLOP/s of the current device."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().linmin_fp32_peak(ctypes.byref(a), ctypes.byref(b), _stream_ptr(stream)))
+    return a.value, b.value
 
 
 def linmin_get_lanes(h) -> int:
