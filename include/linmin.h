@@ -255,6 +255,16 @@ LINMIN_API linmin_status linmin_autotune(linmin_handle h, const float *cube, lon
 /* Library version string. */
 LINMIN_API const char *linmin_version(void);
 
+/* Device allocations the library's handles hold now, over all devices
+ * (handles of servers included).  With the environment variable
+ * LINMIN_FAIL_ALLOC = N (N >= 1), read when a handle is created, that
+ * handle's N-th device allocation fails as if the device were out of
+ * memory, without calling CUDA (linmin_autofit: its allocation, for
+ * N = 1): the entry point returns LINMIN_ERR_OOM, and this count shows
+ * that nothing was kept.  Unset or 0: no injection.  The paper has no
+ * counterpart: a diagnostic for the error paths. */
+LINMIN_API linmin_status linmin_live_allocations(long long *count);
+
 /* Measured FP32 throughput of the current device, the roofline peak of the
  * interior-point solve (which is bound by FP32 FMAs): TFLOP/s (2 flops
  * per FMA) of independent FMA chains on every SM, as scalar FFMA
@@ -313,6 +323,9 @@ typedef struct {
     unsigned long long handles_created, evictions;
     unsigned long long bytes, peak_bytes;  /* device bytes of handles: now / at most */
     int running, max_running;              /* chunks on the device: now / at most */
+    long long libraries;                   /* distinct libraries kept (at most 64 beyond
+                                              those in use: the least recently used idle
+                                              ones are dropped with their handles) */
 } linmin_server_stats;
 
 LINMIN_API linmin_status linmin_server_default_options(linmin_server_options *opt);
@@ -480,16 +493,19 @@ LINMIN_API linmin_status linmin_detect(const float *x, const float *sx, const fl
                                        linmin_detection *out, void *stream);
 
 /* Sums over the pixels where mineral i is present (pos) and absent (neg)
- * in a synthetic cube, for eq. Threshold (device memory). */
+ * in a synthetic cube, for eq. Threshold (device memory): counts, sums,
+ * and sums of squared deviations from the mean (m2; two passes, so the
+ * variance m2 / n has no cancellation). */
 typedef struct {
     long long n_pos[LINMIN_MAX_P], n_neg[LINMIN_MAX_P];
-    double sum_pos[LINMIN_MAX_P], sumsq_pos[LINMIN_MAX_P];
-    double sum_neg[LINMIN_MAX_P], sumsq_neg[LINMIN_MAX_P];
+    double sum_pos[LINMIN_MAX_P], m2_pos[LINMIN_MAX_P];
+    double sum_neg[LINMIN_MAX_P], m2_neg[LINMIN_MAX_P];
 } linmin_threshold_sums;
 
 /* Accumulate linmin_threshold_sums of x (device, N x P) split by truth
  * (device, N bit masks), for minerals i < n_minerals; out is device
- * memory, overwritten.  Same limits as linmin_detect. */
+ * memory, overwritten.  Two stream-ordered launches (sums, then squared
+ * deviations from their means).  Same limits as linmin_detect. */
 LINMIN_API linmin_status linmin_threshold_stats(const float *x, const unsigned long long *truth,
                                                 long long N, int P, int n_minerals,
                                                 linmin_threshold_sums *out, void *stream);

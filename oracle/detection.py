@@ -92,12 +92,13 @@ def detect(x, sx=None, rms=None, iterations=None, truth=None, x_min=None,
 
 
 def threshold_sums(x, truth, n_minerals: int) -> dict:
-    """Counts, sums and sums of squares (fp64) of x[:, i] over the pixels
-    where mineral i is present (pos) and absent (neg)."""
+    """Counts, sums and sums of squared deviations from the mean (fp64) of
+    x[:, i] over the pixels where mineral i is present (pos) and absent
+    (neg)."""
     x = np.asarray(x, dtype=np.float32).astype(np.float64)
     t = np.asarray(truth, dtype=np.uint64)
     P = x.shape[1]
-    keys = ("n_pos", "n_neg", "sum_pos", "sumsq_pos", "sum_neg", "sumsq_neg")
+    keys = ("n_pos", "n_neg", "sum_pos", "m2_pos", "sum_neg", "m2_neg")
     out = {k: np.zeros(P, np.int64 if k.startswith("n_") else np.float64) for k in keys}
     for i in range(n_minerals):
         pres = ((t >> np.uint64(i)) & np.uint64(1)).astype(bool)
@@ -105,7 +106,7 @@ def threshold_sums(x, truth, n_minerals: int) -> dict:
             v = x[sel, i]
             out["n_" + name][i] = v.size
             out["sum_" + name][i] = v.sum()
-            out["sumsq_" + name][i] = (v * v).sum()
+            out["m2_" + name][i] = ((v - v.mean()) ** 2).sum() if v.size else 0.0
     return out
 
 

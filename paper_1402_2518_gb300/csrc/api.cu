@@ -17,8 +17,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -31,6 +33,7 @@
 using namespace lm;
 
 struct linmin_ctx {
+    long long fail_at = 0, n_alloc = 0;  // allocation-failure injection (LINMIN_FAIL_ALLOC)
     int L = 0, P = 0;                  // P: spectra of the internal problem
     // slo / pos: the caller's P is P - 1 (the last internal spectrum is the
     // zero slack spectrum), results scaled by M (LINMIN_POS_SCALE for pos)
@@ -157,12 +160,32 @@ static void pool_release(int dev)
     if (--ps.live == 0 && ps.pool) cudaMemPoolTrimTo(ps.pool, 0);
 }
 
+// Device allocations the handles hold now (all devices); with
+// LINMIN_FAIL_ALLOC the error paths are checked against it for leaks.
+static std::atomic<long long> g_live_allocs{0};
+
+// Allocation-failure injection, to exercise the error paths on the host
+// (no GPU fault): LINMIN_FAIL_ALLOC = N >= 1, read when a handle is
+// created, makes that handle's N-th device allocation fail with
+// cudaErrorMemoryAllocation without calling CUDA.  Unset or 0: off.
+long long lm::injected_alloc_failure()
+{
+    const char *e = std::getenv("LINMIN_FAIL_ALLOC");
+    if (!e) return 0;
+    const long long v = std::atoll(e);
+    return v > 0 ? v : 0;
+}
+
 template <typename T>
 static cudaError_t dalloc(linmin_ctx *h, T **p, size_t n)
 {
-    if (*p) { cudaFreeAsync(*p, h->stream); *p = nullptr; }
+    if (*p) { cudaFreeAsync(*p, h->stream); *p = nullptr; --g_live_allocs; }
     if (n == 0) n = 1;
-    return cudaMallocFromPoolAsync((void **)p, n * sizeof(T), h->pool, h->stream);
+    if (h->fail_at > 0 && ++h->n_alloc == h->fail_at) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocFromPoolAsync((void **)p, n * sizeof(T), h->pool, h->stream);
+    if (e == cudaSuccess) ++g_live_allocs;
+    else *p = nullptr;
+    return e;
 }
 
 // rank [S^T; 1^T] == P in fp64 (modified Gram-Schmidt with one
@@ -741,6 +764,13 @@ int linmin_get_lanes(linmin_handle h)
     return h ? h->bucket.G : -1;
 }
 
+linmin_status linmin_live_allocations(long long *count)
+{
+    if (!count) return LINMIN_ERR_INVALID;
+    *count = g_live_allocs.load();
+    return LINMIN_OK;
+}
+
 linmin_status linmin_set_lanes(linmin_handle h, int lanes)
 {
     if (!h) return fail(nullptr, LINMIN_ERR_INVALID, "handle is NULL");
@@ -845,6 +875,7 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
     linmin_ctx *h = new linmin_ctx();
     h->L = L; h->P = P; h->user_P = P; h->opt = o;
     h->stream = (cudaStream_t)o.cuda_stream;
+    h->fail_at = injected_alloc_failure();
     cudaGetDevice(&h->device);
     if (!ipm_bucket(P, &h->bucket)) { delete h; return fail(nullptr, LINMIN_ERR_UNSUPPORTED, "P"); }
     cudaError_t a = pool_acquire(h->device, &h->pool);
@@ -907,7 +938,7 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT, h->bsl,
                     h->fexp, h->xa, h->sxa};
     for (void *p : ptrs)
-        if (p) cudaFreeAsync(p, h->stream);
+        if (p) { cudaFreeAsync(p, h->stream); --g_live_allocs; }
     if (h->cstream) {
         cudaStreamSynchronize(h->cstream);
         cudaStreamDestroy(h->cstream);

@@ -34,4 +34,8 @@ linmin_status reserve(linmin_handle h, long long N, bool host_io);
 // without a handle).
 void set_global_error(const std::string &m);
 
+// N >= 1 when LINMIN_FAIL_ALLOC = N asks for the N-th device allocation of
+// a handle (or of a call that allocates on its own) to fail; else 0.
+long long injected_alloc_failure();
+
 }  // namespace lm

@@ -330,7 +330,9 @@ extern "C" linmin_status linmin_autofit(const float *library, int L, int P, floa
     if (e != cudaSuccess)
         return af_err(LINMIN_ERR_CUDA, std::string("linmin_autofit: ") + cudaGetErrorString(e));
     double *q = nullptr;
-    e = cudaMallocAsync(&q, (size_t)P * P * L * sizeof(double), s);
+    e = lm::injected_alloc_failure() == 1
+            ? cudaErrorMemoryAllocation
+            : cudaMallocAsync(&q, (size_t)P * P * L * sizeof(double), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return af_err(e == cudaErrorMemoryAllocation ? LINMIN_ERR_OOM : LINMIN_ERR_CUDA,

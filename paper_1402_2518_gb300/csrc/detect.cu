@@ -193,6 +193,7 @@ struct StatsArgs {
     long long N;
     int P, nm;
     linmin_threshold_sums *out;
+    int pass;          // 0: counts and sums; 1: squared deviations from the pass-0 means
 };
 
 __global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
@@ -201,6 +202,19 @@ __global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
     const int P = a.P, nm = a.nm;
     long long np[2] = {0, 0}, nn[2] = {0, 0};
     double sp[2] = {0.0, 0.0}, qp[2] = {0.0, 0.0}, sn[2] = {0.0, 0.0}, qn[2] = {0.0, 0.0};
+    // pass 1: the means of pass 0 (complete: same stream), subtracted
+    // before squaring, so the variance has no cancellation
+    double mp[2] = {0.0, 0.0}, mn[2] = {0.0, 0.0};
+    if (a.pass == 1) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = lane + 32 * h;
+            if (i >= nm) continue;
+            const long long cp = a.out->n_pos[i], cn = a.out->n_neg[i];
+            mp[h] = cp ? a.out->sum_pos[i] / (double)cp : 0.0;
+            mn[h] = cn ? a.out->sum_neg[i] / (double)cn : 0.0;
+        }
+    }
     long long n0, n1;
     warp_range(a.N, n0, n1);
     for (long long n = n0; n < n1; ++n) {
@@ -211,8 +225,15 @@ __global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
             const int i = lane + 32 * h;
             if (i >= nm) continue;
             const double v = (double)__ldg(xr + i);
-            if ((t >> i) & 1ull) { ++np[h]; sp[h] += v; qp[h] += v * v; }
-            else                 { ++nn[h]; sn[h] += v; qn[h] += v * v; }
+            if ((t >> i) & 1ull) {
+                ++np[h];
+                if (a.pass == 0) sp[h] += v;
+                else qp[h] += (v - mp[h]) * (v - mp[h]);
+            } else {
+                ++nn[h];
+                if (a.pass == 0) sn[h] += v;
+                else qn[h] += (v - mn[h]) * (v - mn[h]);
+            }
         }
     }
     __shared__ long long s_np[DTH / 32][LINMIN_MAX_P], s_nn[DTH / 32][LINMIN_MAX_P];
@@ -234,15 +255,18 @@ __global__ void __launch_bounds__(DTH) threshold_stats_kernel(StatsArgs a)
         tsp += s_sp[q][i]; tqp += s_qp[q][i]; tsn += s_sn[q][i]; tqn += s_qn[q][i];
     }
     linmin_threshold_sums *o = a.out;
-    if (tnp) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)tnp);
-        atomicAdd(&o->sum_pos[i], tsp);
-        atomicAdd(&o->sumsq_pos[i], tqp);
-    }
-    if (tnn) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)tnn);
-        atomicAdd(&o->sum_neg[i], tsn);
-        atomicAdd(&o->sumsq_neg[i], tqn);
+    if (a.pass == 0) {
+        if (tnp) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_pos[i]), (unsigned long long)tnp);
+            atomicAdd(&o->sum_pos[i], tsp);
+        }
+        if (tnn) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&o->n_neg[i]), (unsigned long long)tnn);
+            atomicAdd(&o->sum_neg[i], tsn);
+        }
+    } else {
+        if (tnp) atomicAdd(&o->m2_pos[i], tqp);
+        if (tnn) atomicAdd(&o->m2_neg[i], tqn);
     }
 }
 
@@ -372,9 +396,12 @@ linmin_status linmin_threshold_stats(const float *x, const unsigned long long *t
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(linmin_threshold_sums), s);
     if (e != cudaSuccess) return cuda_err(e, "linmin_threshold_stats: memset");
     if (N > 0 && n_minerals > 0) {
-        StatsArgs a{x, truth, N, P, n_minerals, out};
-        threshold_stats_kernel<<<grid_for(N), DTH, 0, s>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "linmin_threshold_stats: launch");
+        for (int pass = 0; pass < 2; ++pass) {
+            StatsArgs a{x, truth, N, P, n_minerals, out, pass};
+            threshold_stats_kernel<<<grid_for(N), DTH, 0, s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return cuda_err(e, "linmin_threshold_stats: launch");
+        }
     }
     return LINMIN_OK;
 }
@@ -387,8 +414,8 @@ linmin_status linmin_thresholds(const linmin_threshold_sums *st, int n_minerals,
         const long long np = st->n_pos[i], nn = st->n_neg[i];
         if (np <= 0 || nn <= 0) { c_out[i] = NAN; continue; }
         const double mp = st->sum_pos[i] / (double)np, mn = st->sum_neg[i] / (double)nn;
-        const double vp = std::max(0.0, st->sumsq_pos[i] / (double)np - mp * mp);
-        const double vn = std::max(0.0, st->sumsq_neg[i] / (double)nn - mn * mn);
+        const double vp = std::max(0.0, st->m2_pos[i] / (double)np);
+        const double vn = std::max(0.0, st->m2_neg[i] / (double)nn);
         c_out[i] = (float)(0.5 * (mp - 2.0 * std::sqrt(vp) + mn + 6.0 * std::sqrt(vn)));
     }
     return LINMIN_OK;

@@ -39,10 +39,17 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Library {
-    uint64_t key = 0;                // content hash with L, P
+    uint64_t key = 0;                // content hash with L, P (probed past collisions)
     int L = 0, P = 0;
     std::vector<float> host;         // checked copy (P x L)
+    std::chrono::steady_clock::time_point last;   // last submit that used it
 };
+
+// Libraries kept by a server beyond those in use: the least recently used
+// unreferenced ones (and the idle worker handles made from them) are
+// dropped above this count.
+constexpr size_t kMaxLibraries = 64;
+constexpr uint64_t kHostIoKey = 0x9e3779b97f4a7c15ULL;   // worker-handle key of host-buffer requests
 
 struct Request {
     long long ticket = 0;
@@ -140,6 +147,39 @@ bool make_room(linmin_server_s *s, size_t need)
     return true;
 }
 
+// Keep at most kMaxLibraries libraries: drop the least recently used ones
+// that no request holds and for which no worker handle is busy, with the
+// idle worker handles made from them (a later library may reuse the key).
+// Caller holds s->mu.
+void evict_libraries(linmin_server_s *s)
+{
+    while (s->libs.size() > kMaxLibraries) {
+        auto victim = s->libs.end();
+        for (auto it = s->libs.begin(); it != s->libs.end(); ++it) {
+            if (it->second.use_count() > 1) continue;            // a request holds it
+            bool busy = false;
+            for (auto &w : s->workers)
+                for (uint64_t k : {it->first, it->first ^ kHostIoKey}) {
+                    auto h = w->handles.find(k);
+                    if (h != w->handles.end() && h->second.busy) busy = true;
+                }
+            if (busy) continue;
+            if (victim == s->libs.end() || it->second->last < victim->second->last) victim = it;
+        }
+        if (victim == s->libs.end()) return;                      // all in use
+        for (auto &w : s->workers)
+            for (uint64_t k : {victim->first, victim->first ^ kHostIoKey}) {
+                auto h = w->handles.find(k);
+                if (h == w->handles.end()) continue;
+                s->bytes -= h->second.bytes;
+                ++s->st.evictions;
+                lm::destroy_async(h->second.h);
+                w->handles.erase(h);
+            }
+        s->libs.erase(victim);
+    }
+}
+
 // Mark a request finished and wake its waiters.  Caller holds s->mu.
 void finish(linmin_server_s *s, Request *rq)
 {
@@ -159,7 +199,7 @@ bool take_chunk(Worker *w, std::shared_ptr<Request> *req, long long *first, long
     for (size_t qi = 0; qi < s->queue.size();) {
         std::shared_ptr<Request> rq = s->queue[qi];
         if (rq->next >= rq->r.N) { ++qi; continue; }       // all chunks handed out
-        const uint64_t key = rq->lib->key ^ (rq->host_io ? 0x9e3779b97f4a7c15ULL : 0);
+        const uint64_t key = rq->lib->key ^ (rq->host_io ? kHostIoKey : 0);
         auto it = w->handles.find(key);
         if (it != w->handles.end() && it->second.cap < rq->chunk) {
             // a cached handle with a smaller reservation: grow it within the budget
@@ -358,13 +398,21 @@ linmin_status linmin_server_submit(linmin_server s, const linmin_request *req, l
     rq->chunk = chunk;
 
     std::lock_guard<std::mutex> g(s->mu);
+    // a hit must hold the same library, not only the same hash: on a
+    // collision, probe the next key
     auto li = s->libs.find(key);
+    while (li != s->libs.end() &&
+           !(li->second->L == r.L && li->second->P == r.P && li->second->host == host))
+        li = s->libs.find(++key);
     if (li == s->libs.end()) {
         auto lib = std::make_shared<Library>();
         lib->key = key; lib->L = r.L; lib->P = r.P; lib->host = std::move(host);
         li = s->libs.emplace(key, lib).first;
     }
+    li->second->last = Clock::now();
     rq->lib = li->second;
+    evict_libraries(s);
+    s->st.libraries = (long long)s->libs.size();
     rq->ticket = s->next_ticket++;
     *ticket = rq->ticket;
     s->all[rq->ticket] = rq;

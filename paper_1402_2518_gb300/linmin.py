@@ -41,7 +41,8 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_get_lanes", "linmin_set_lanes", "linmin_autotune", "linmin_unmix_cov",
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
             "linmin_thresholds", "linmin_autofit", "linmin_second_pass",
-            "linmin_unmix_masked", "linmin_noalloc_scratch_bytes", "linmin_fp32_peak")
+            "linmin_unmix_masked", "linmin_noalloc_scratch_bytes", "linmin_fp32_peak",
+            "linmin_live_allocations")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -72,7 +73,8 @@ class linmin_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_ulonglong) for n in
                 ("requests", "requests_done", "chunks", "handles_created", "evictions",
                  "bytes", "peak_bytes")] + [("running", ctypes.c_int),
-                                            ("max_running", ctypes.c_int)]
+                                            ("max_running", ctypes.c_int),
+                                            ("libraries", ctypes.c_longlong)]
 
 
 _I64x = ctypes.c_longlong * LINMIN_MAX_P
@@ -86,8 +88,8 @@ class linmin_detection(ctypes.Structure):
 
 
 class linmin_threshold_sums(ctypes.Structure):
-    _fields_ = [("n_pos", _I64x), ("n_neg", _I64x), ("sum_pos", _F64x), ("sumsq_pos", _F64x),
-                ("sum_neg", _F64x), ("sumsq_neg", _F64x)]
+    _fields_ = [("n_pos", _I64x), ("n_neg", _I64x), ("sum_pos", _F64x), ("m2_pos", _F64x),
+                ("sum_neg", _F64x), ("m2_neg", _F64x)]
 
 
 class LinminError(RuntimeError):
@@ -136,6 +138,8 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_fp32_peak.argtypes = [ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     lib.linmin_fp32_peak.restype = ctypes.c_int
+    lib.linmin_live_allocations.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+    lib.linmin_live_allocations.restype = ctypes.c_int
     SV = ctypes.c_void_p
     lib.linmin_server_default_options.argtypes = [ctypes.POINTER(linmin_server_options)]
     lib.linmin_server_default_options.restype = ctypes.c_int
@@ -310,6 +314,13 @@ def linmin_noalloc_scratch_bytes(L: int, P: int, N: int) -> tuple[int, int]:
     b = ctypes.c_ulonglong(0)
     st = lib().linmin_noalloc_scratch_bytes(int(L), int(P), int(N), ctypes.byref(b))
     return st, int(b.value)
+
+
+def linmin_live_allocations() -> int:
+    """Device allocations the library's handles hold now."""
+    n = ctypes.c_longlong(0)
+    _check(lib().linmin_live_allocations(ctypes.byref(n)))
+    return n.value
 
 
 def linmin_fp32_peak(stream=None) -> tuple[float, float]:

@@ -104,7 +104,7 @@ def test_threshold_sums_and_eq_threshold(pkg, N, P, nm):
     ref = od.threshold_sums(x, truth, nm)
     for k in ("n_pos", "n_neg"):
         np.testing.assert_array_equal(np.array(getattr(sums, k))[:P], ref[k])
-    for k in ("sum_pos", "sumsq_pos", "sum_neg", "sumsq_neg"):
+    for k in ("sum_pos", "m2_pos", "sum_neg", "m2_neg"):
         np.testing.assert_allclose(np.array(getattr(sums, k))[:P], ref[k], rtol=1e-12, atol=1e-300)
     C = pkg.linmin_thresholds(sums, nm)
     Cref = od.thresholds(x, truth, nm).astype(np.float32)
@@ -158,3 +158,27 @@ def test_surface_mixtures_end_to_end(pkg):
     fd = got["false_pos"][:nm].sum() / (N * nm - got["n_true"][:nm].sum())
     print(f"surface mixtures: positive detection {pd:.3f}, false detection {fd:.4f}")
     assert pd > 0.5 and fd < 0.1
+
+
+def test_threshold_variance_without_cancellation(pkg):
+    """eq. Threshold's standard deviations where the mean is ~1e7 times the
+    standard deviation (abundances 0.5 + a few float32 ulps): sums of
+    squares minus the squared mean would cancel to noise; the two-pass
+    statistics give the numpy standard deviation."""
+    from paper_1402_2518_gb300 import linmin
+    rng = np.random.Generator(np.random.PCG64(4242))
+    N, P, nm = 65536, 36, 32
+    ulp = np.float32(2.0 ** -24)
+    truth = np.zeros(N, np.uint64)
+    x = np.zeros((N, P), np.float32)
+    for i in range(nm):
+        pres = rng.random(N) < 0.3
+        truth[pres] |= np.uint64(1) << np.uint64(i)
+        x[pres, i] = np.float32(0.5) + ulp * rng.integers(-3, 4, pres.sum()).astype(np.float32)
+        x[~pres, i] = np.float32(0.25) + ulp * rng.integers(-2, 3, (~pres).sum()).astype(np.float32)
+    buf = torch.zeros((ctypes.sizeof(linmin.linmin_threshold_sums),), dtype=torch.uint8, device=DEV)
+    pkg.linmin_threshold_stats(_dev(x), _dev(truth), N, P, nm, buf)
+    torch.cuda.synchronize()
+    C = pkg.linmin_thresholds(pkg.threshold_sums(buf), nm)
+    Cref = od.thresholds(x, truth, nm)
+    np.testing.assert_allclose(C, Cref.astype(np.float32), rtol=1e-6)

@@ -154,3 +154,26 @@ def test_bad_requests_refused(pkg):
     t = server.submit(cube.S, cube.X[:0], cube.sigma)           # N = 0: done at once
     assert server.wait(t)[0] == 0
     server.close()
+
+
+def test_library_cache_stays_bounded(pkg):
+    """A long-running server that sees many libraries keeps at most 64 of the
+    idle ones (with their handles); a library met again after eviction is
+    loaded again, and every result still equals the cube unmixed alone."""
+    srv = pkg.Server(hbm_budget_bytes=8 << 30, slots=2, chunk_pixels=4096)
+    try:
+        cubes = [synth.random_instance(7400 + i, 64, 40, 8, n_extras=0) for i in range(70)]
+        cubes.append(cubes[0])                 # the first library again, after eviction
+        for cube in cubes:
+            out = _outputs(cube.N, cube.P, True)
+            t = srv.submit(torch.from_numpy(cube.S).to(DEV), torch.from_numpy(cube.X).to(DEV),
+                           torch.from_numpy(cube.sigma).to(DEV), *out)
+            st, _ = srv.wait(t)
+            assert st == 0
+            st_a, ref = _alone(pkg, cube)
+            for got, want in zip(out, ref):
+                np.testing.assert_array_equal(_host(got), want)
+            assert srv.stats()["libraries"] <= 64
+        assert srv.stats()["evictions"] > 0
+    finally:
+        srv.close()
