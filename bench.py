@@ -327,7 +327,7 @@ def _pct(v, q):
 
 
 def run_serving(pkg, dev, n_cubes: int, rate: float, budget_gb: float, slots: int,
-                chunk: int):
+                chunk: int, fp32_peak: float = 80.0):
     """Serving stream of uneven cubes through the library's server (chunks of
     all requests in flight on `slots` streams) against the plain path: one
     linmin_unmix call per cube, one after the other.  Inputs and outputs are
@@ -402,7 +402,25 @@ def run_serving(pkg, dev, n_cubes: int, rate: float, budget_gb: float, slots: in
            "hbm_budget_gb": budget_gb, "inputs": "device-resident"}
     res["stream"] = served(arrivals)
     res["stream_plain"] = plain(arrivals)
+    # a stream whose arrivals outrun the server (10x the rate): pixels/s is
+    # then the server's capacity, not the arrival process
+    sat_rate = 10.0 * rate
+    sat = synth.poisson_arrivals(n_cubes, sat_rate)
+    res["saturated_rate_per_s"] = sat_rate
+    res["stream_saturated"] = served(sat)
+    res["stream_saturated_plain"] = plain(sat)
     res["batch"] = served(np.zeros(n_cubes))
+    # interior-point flops of the batch (each cube's own iteration counts,
+    # P^3 / 3 + 6 P^2 per pixel-iteration) over its makespan
+    flops = 0.0
+    for (S, X, sg, N, P), o in zip(cubes, outs):
+        flops += float(o[3].to(torch.float64).abs().sum().item()) * (P ** 3 / 3.0 + 6.0 * P * P)
+    res["batch"]["roofline"] = {"kernel": "interior point, all cubes", "bound": "alu",
+                                "achieved": flops / res["batch"]["makespan_s"] / 1e12,
+                                "peak": fp32_peak, "unit": "TFLOP/s",
+                                "frac": flops / res["batch"]["makespan_s"] / 1e12 / fp32_peak,
+                                "note": "whole-call makespan (projection, crossover and RMS "
+                                        "included): a lower bound of the solve's fraction"}
     res["batch_plain"] = plain(np.zeros(n_cubes))
     res["plain_note"] = ("one linmin_unmix per cube, sequential, handles created before "
                          "the timed stream")
@@ -733,7 +751,7 @@ def main():
     serving = None
     if not args.no_serving and rank == 0:
         serving = run_serving(pkg, dev, args.serving_cubes, args.serving_rate,
-                              args.serving_budget_gb, args.serving_slots, args.serving_chunk)
+                              args.serving_budget_gb, args.serving_slots, args.serving_chunk, fp32_peak)
     if rank != 0:
         dist.barrier() if ws > 1 else None
         return

@@ -301,6 +301,10 @@ typedef struct {
     int slots;                /* worker streams = chunks in flight (1..64, default 4) */
     long long chunk_pixels;   /* pixels per chunk (default 65536) */
     int max_iter;             /* interior-point cap per pixel (default 100) */
+    int autotune;             /* != 0 (default): the first handle made for a library
+                                 shape (L, P) on a device runs linmin_autotune on its
+                                 first chunk, and later handles of that shape (in any
+                                 server of the process) take its choice */
 } linmin_server_options;
 
 /* One cube.  Pointers as in linmin_create / linmin_unmix (host or device;
@@ -326,6 +330,8 @@ typedef struct {
     long long libraries;                   /* distinct libraries kept (at most 64 beyond
                                               those in use: the least recently used idle
                                               ones are dropped with their handles) */
+    long long autotuned;                   /* autotuner runs by this server (one per
+                                              shape and device in the process) */
 } linmin_server_stats;
 
 LINMIN_API linmin_status linmin_server_default_options(linmin_server_options *opt);

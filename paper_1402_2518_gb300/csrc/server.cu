@@ -29,6 +29,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "api_internal.h"
@@ -71,6 +72,7 @@ struct Entry {                       // a worker's handle for one library
     size_t bytes = 0;
     long long cap = 0;               // pixels its scratch is reserved for
     bool busy = false;
+    bool tune = false;               // run the autotuner on its first chunk
     Clock::time_point last;
 };
 
@@ -103,6 +105,12 @@ struct Worker {
     std::map<uint64_t, Entry> handles;   // by library key (mixed with host_io)
     std::thread th;
 };
+
+// Autotuned lanes per pixel by (device, L, P), shared by every server of
+// the process (the choice depends on the GPU and the shape only): 0 while
+// one handle is being tuned (the others use the default table meanwhile).
+std::mutex g_lanes_mu;
+std::map<std::tuple<int, int, int>, int> g_lanes;
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ULL)
 {
@@ -246,6 +254,16 @@ bool take_chunk(Worker *w, std::shared_ptr<Request> *req, long long *first, long
                 ++qi;
                 continue;
             }
+            if (s->opt.autotune) {
+                std::lock_guard<std::mutex> g(g_lanes_mu);
+                auto lt = g_lanes.find({s->device, rq->r.L, rq->r.P});
+                if (lt == g_lanes.end()) {                   // first of its shape: tune it
+                    g_lanes[{s->device, rq->r.L, rq->r.P}] = 0;
+                    e.tune = true;
+                } else if (lt->second > 0) {
+                    linmin_set_lanes(e.h, lt->second);
+                }
+            }
             e.bytes = need;
             e.cap = rq->chunk;
             s->bytes += need;
@@ -282,10 +300,30 @@ void run_worker(Worker *w)
         ++s->st.running;
         s->st.max_running = std::max(s->st.max_running, s->st.running);
         linmin_handle h = e->h;
+        const bool tune = e->tune;
+        e->tune = false;
         lk.unlock();
 
         const linmin_request &r = rq->r;
         const size_t P = r.P, L = r.L, f = (size_t)first;
+        if (tune) {
+            // the autotuner on this chunk's pixels (synchronous, on the
+            // worker's stream, outside the lock); its choice serves every
+            // later handle of the shape
+            int lanes = 0;
+            const bool ok =
+                linmin_autotune(h, r.cube + f * L, n, r.sigma, &lanes, nullptr, 0, nullptr) ==
+                LINMIN_OK;
+            {
+                std::lock_guard<std::mutex> g(g_lanes_mu);
+                if (ok) g_lanes[{s->device, r.L, r.P}] = lanes;
+                else g_lanes.erase({s->device, r.L, r.P});   // a later handle tries again
+            }
+            if (ok) {
+                std::lock_guard<std::mutex> g(s->mu);
+                ++s->st.autotuned;
+            }
+        }
         linmin_status st = linmin_unmix(
             h, r.cube + f * L, n, r.sigma, r.abundances ? r.abundances + f * P : nullptr,
             r.uncertainties ? r.uncertainties + f * P : nullptr,
@@ -330,6 +368,7 @@ linmin_status linmin_server_default_options(linmin_server_options *opt)
     opt->slots = 4;
     opt->chunk_pixels = 65536;
     opt->max_iter = 100;
+    opt->autotune = 1;
     return LINMIN_OK;
 }
 

@@ -59,7 +59,8 @@ class linmin_options(ctypes.Structure):
 
 class linmin_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_ulonglong), ("slots", ctypes.c_int),
-                ("chunk_pixels", ctypes.c_longlong), ("max_iter", ctypes.c_int)]
+                ("chunk_pixels", ctypes.c_longlong), ("max_iter", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class linmin_request(ctypes.Structure):
@@ -74,7 +75,8 @@ class linmin_server_stats(ctypes.Structure):
                 ("requests", "requests_done", "chunks", "handles_created", "evictions",
                  "bytes", "peak_bytes")] + [("running", ctypes.c_int),
                                             ("max_running", ctypes.c_int),
-                                            ("libraries", ctypes.c_longlong)]
+                                            ("libraries", ctypes.c_longlong),
+                                            ("autotuned", ctypes.c_longlong)]
 
 
 _I64x = ctypes.c_longlong * LINMIN_MAX_P
@@ -582,8 +584,11 @@ class Server:
     its ticket is waited on (the C side reads and writes them meanwhile)."""
 
     def __init__(self, hbm_budget_bytes: int | None = None, slots: int | None = None,
-                 chunk_pixels: int | None = None, max_iter: int | None = None):
+                 chunk_pixels: int | None = None, max_iter: int | None = None,
+                 autotune: bool | None = None):
         o = linmin_server_default_options()
+        if autotune is not None:
+            o.autotune = int(bool(autotune))
         if hbm_budget_bytes is not None:
             o.hbm_budget_bytes = int(hbm_budget_bytes)
         if slots is not None:

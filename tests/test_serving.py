@@ -80,7 +80,7 @@ def test_mixed_stream_equals_alone(pkg):
     cubes = _cubes()
     rng = np.random.Generator(np.random.PCG64(11))
     gaps = rng.exponential(1.0 / 200.0, len(cubes))          # Poisson arrivals, 200/s
-    server = pkg.Server(slots=4, chunk_pixels=4096)
+    server = pkg.Server(slots=4, chunk_pixels=4096, autotune=False)
     res = _run_stream(pkg, cubes, server, gaps)
     stats = server.stats()
     server.close()
@@ -99,7 +99,7 @@ def test_mixed_stream_equals_alone(pkg):
 def test_mixed_stream_matches_oracle(pkg):
     """Sampled pixels of two cubes of the mix against the FP64 oracle."""
     cubes = _cubes()
-    server = pkg.Server(slots=3, chunk_pixels=2048)
+    server = pkg.Server(slots=3, chunk_pixels=2048, autotune=False)
     res = _run_stream(pkg, cubes, server, [0.0] * len(cubes))
     stats = server.stats()
     server.close()
@@ -121,7 +121,7 @@ def test_small_budget_admission(pkg):
              for i in range(6)]
     one = pkg.linmin_server_handle_bytes(184, 36, 1024, host_io=True)
     budget = int(2.5 * one)
-    server = pkg.Server(hbm_budget_bytes=budget, slots=4, chunk_pixels=1024)
+    server = pkg.Server(hbm_budget_bytes=budget, slots=4, chunk_pixels=1024, autotune=False)
     res = _run_stream(pkg, cubes, server, [0.0] * len(cubes))
     stats = server.stats()
     server.close()
@@ -160,7 +160,7 @@ def test_library_cache_stays_bounded(pkg):
     """A long-running server that sees many libraries keeps at most 64 of the
     idle ones (with their handles); a library met again after eviction is
     loaded again, and every result still equals the cube unmixed alone."""
-    srv = pkg.Server(hbm_budget_bytes=8 << 30, slots=2, chunk_pixels=4096)
+    srv = pkg.Server(hbm_budget_bytes=8 << 30, slots=2, chunk_pixels=4096, autotune=False)
     try:
         cubes = [synth.random_instance(7400 + i, 64, 40, 8, n_extras=0) for i in range(70)]
         cubes.append(cubes[0])                 # the first library again, after eviction
@@ -175,5 +175,32 @@ def test_library_cache_stays_bounded(pkg):
                 np.testing.assert_array_equal(_host(got), want)
             assert srv.stats()["libraries"] <= 64
         assert srv.stats()["evictions"] > 0
+    finally:
+        srv.close()
+
+
+def test_autotuned_server_results(pkg):
+    """With the autotuner on (the default), the first handle of each library
+    shape is tuned on its first chunk and later handles of that shape reuse
+    the choice; results stay within the parity bars of the oracle."""
+    cubes = [synth.random_instance(7600 + i, 3000, L, P, n_extras=4)
+             for i, (L, P) in enumerate([(128, 16), (184, 36), (184, 36), (240, 48)])]
+    srv = pkg.Server(slots=2, chunk_pixels=1024)
+    try:
+        tickets = []
+        outs = []
+        for cube in cubes:
+            out = _outputs(cube.N, cube.P, True)
+            outs.append(out)
+            tickets.append(srv.submit(torch.from_numpy(cube.S).to(DEV),
+                                      torch.from_numpy(cube.X).to(DEV),
+                                      torch.from_numpy(cube.sigma).to(DEV), *out))
+        for t in tickets:
+            assert srv.wait(t)[0] == 0
+        stats = srv.stats()
+        assert stats["autotuned"] <= 3                   # at most once per shape in the process
+        for cube, out in zip(cubes, outs):
+            ref = oracle.unmix(cube.S, cube.sigma, cube.X[:400])
+            assert np.abs(_host(out[0])[:400] - ref["x"]).max() <= 1e-4
     finally:
         srv.close()
