@@ -588,8 +588,8 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
             LM_CUDA(h, launch_project(cin, nk, L, P, h->prep.Bhi, h->prep.Blo, chi, clo, st),
                     "projection kernel");
             ++proj_launches;
-        } else if (h->opt.precision == LINMIN_PROJ_TC && tc2_usable(cin, nk, L)) {
-            LM_CUDA(h, launch_project_tc2(cin, nk, L, P, h->bsl, h->fexp, h->rexp + off, chi, clo,
+        } else if (h->opt.precision == LINMIN_PROJ_TC && tma_projection_usable(cin, nk, L)) {
+            LM_CUDA(h, launch_project_tma(cin, nk, L, P, h->bsl, h->fexp, h->rexp + off, chi, clo,
                                           h->prep.flags, st), "tensor-core projection");
             proj_launches += 2;
         } else {

@@ -67,10 +67,10 @@ cudaError_t launch_project_tc(const float *cube, long long N, int L, int P, int 
                               const __nv_bfloat16 *bsl, const int *fexp, float *c_hi,
                               float *c_lo, int *err, cudaStream_t st);
 // TMA-fed exact projection (per-pixel exponent pass into rexp, N ints,
-// then the pipelined GEMM): usable when rows are 16-byte strided and
+// then the warp-specialised GEMM): usable when rows are 16-byte strided and
 // aligned; otherwise launch_project_tc.
-bool tc2_usable(const float *cube, long long N, int L);
-cudaError_t launch_project_tc2(const float *cube, long long N, int L, int P,
+bool tma_projection_usable(const float *cube, long long N, int L);
+cudaError_t launch_project_tma(const float *cube, long long N, int L, int P,
                                const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st);
 // slo / pos outputs from the slack-augmented internal problem
