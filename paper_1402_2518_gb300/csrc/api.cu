@@ -84,6 +84,10 @@ struct linmin_ctx {
     // host-buffer pipeline: copy stream and its events
     cudaStream_t cstream = nullptr;
     cudaEvent_t pev_in[8] = {}, pev_out[2] = {};
+    // side stream of the tensor-core projection's exponent pass (it needs
+    // only the cube, so it runs while the library is prepared)
+    cudaStream_t xstream = nullptr;
+    cudaEvent_t xev[2] = {};
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -478,6 +482,15 @@ static linmin_status ensure_copy_stream(linmin_ctx *h)
     return LINMIN_OK;
 }
 
+static linmin_status ensure_side_stream(linmin_ctx *h)
+{
+    if (h->xstream) return LINMIN_OK;
+    LM_CUDA(h, cudaStreamCreateWithFlags(&h->xstream, cudaStreamNonBlocking), "side stream");
+    for (cudaEvent_t &e : h->xev)
+        LM_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    return LINMIN_OK;
+}
+
 static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
                                 const double *cov_inv, float *abundances, float *uncertainties,
                                 float *residual_rms, int *iterations,
@@ -557,6 +570,18 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
 
     LM_CUDA(h, cudaMemsetAsync(h->prep.flags, 0, sizeof(int), st), "memset");
     LM_CUDA(h, cudaMemsetAsync(h->dcnt, 0, 8 * sizeof(unsigned long long), st), "memset");
+    // exact tensor-core projection of a resident cube: its exponent pass
+    // goes on the side stream, after the work queued so far, concurrent
+    // with the library preparation below
+    const bool tma_proj = h->opt.precision == LINMIN_PROJ_TC && tma_projection_usable(d_cube, N, L);
+    const bool side_exp = tma_proj && !piped;
+    if (side_exp) {
+        if ((s = ensure_side_stream(h)) != LINMIN_OK) return s;
+        LM_CUDA(h, cudaEventRecord(h->xev[0], st), "event");
+        LM_CUDA(h, cudaStreamWaitEvent(h->xstream, h->xev[0], 0), "event wait");
+        LM_CUDA(h, launch_rowexp(d_cube, N, L, h->rexp, h->xstream), "exponent pass");
+        LM_CUDA(h, cudaEventRecord(h->xev[1], h->xstream), "event");
+    }
     mark(h, 0);
     if (cov_inv)
         LM_CUDA(h, launch_prep_cov(h->dS, h->cov, L, P, h->bucket.PP, h->prep, h->covT, st),
@@ -566,12 +591,9 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     mark(h, 1);
     int proj_launches = 0;
     if (h->opt.precision != LINMIN_PROJ_DF) {
-        if (!cov_inv) {
-            LM_CUDA(h, launch_prep_t_diag(h->dS, d_sigma, L, P, h->covT, st), "projection prep");
-            ++proj_launches;
-        }
-        LM_CUDA(h, launch_tc_prep(h->covT, L, P, h->prep.scale, h->opt.precision, h->bsl, h->fexp,
-                                  st), "projection prep");
+        LM_CUDA(h, launch_tc_prep(h->dS, d_sigma, cov_inv ? h->covT : nullptr, L, P,
+                                  h->prep.scale, h->opt.precision, h->bsl, h->fexp, st),
+                "projection prep");
         proj_launches += h->opt.precision == LINMIN_PROJ_TC ? 2 : 1;
     }
     // the projection, piece by piece as the cube arrives when piped
@@ -588,7 +610,11 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
             LM_CUDA(h, launch_project(cin, nk, L, P, h->prep.Bhi, h->prep.Blo, chi, clo, st),
                     "projection kernel");
             ++proj_launches;
-        } else if (h->opt.precision == LINMIN_PROJ_TC && tma_projection_usable(cin, nk, L)) {
+        } else if (tma_proj) {
+            if (side_exp)
+                LM_CUDA(h, cudaStreamWaitEvent(st, h->xev[1], 0), "event wait");
+            else
+                LM_CUDA(h, launch_rowexp(cin, nk, L, h->rexp + off, st), "exponent pass");
             LM_CUDA(h, launch_project_tma(cin, nk, L, P, h->bsl, h->fexp, h->rexp + off, chi, clo,
                                           h->prep.flags, st), "tensor-core projection");
             proj_launches += 2;
@@ -927,6 +953,8 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
 linmin_status lm::destroy_async(linmin_handle h)
 {
     if (!h) return LINMIN_OK;
+    // the side stream may still write rexp if a call failed before joining it
+    if (h->xstream) cudaStreamSynchronize(h->xstream);
     for (auto &set : h->ev)
         for (cudaEvent_t e : set)
             if (e) cudaEventDestroy(e);
@@ -943,6 +971,9 @@ linmin_status lm::destroy_async(linmin_handle h)
         cudaStreamSynchronize(h->cstream);
         cudaStreamDestroy(h->cstream);
     }
+    if (h->xstream) cudaStreamDestroy(h->xstream);
+    for (cudaEvent_t e : h->xev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : h->pev_in)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : h->pev_out)

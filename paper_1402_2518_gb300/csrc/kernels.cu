@@ -180,28 +180,6 @@ __global__ void prep_b_cov_kernel(const double *__restrict__ T, int L, int P, in
     }
 }
 
-// T = W^2 S^T (L x P fp64) for the tensor-core projection of the per-band case
-__global__ void prep_t_diag_kernel(const float *__restrict__ S, const float *__restrict__ sigma,
-                                   int L, int P, double *__restrict__ T)
-{
-    const long long total = (long long)L * P;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int l = (int)(e / P), j = (int)(e % P);
-        const double sg = (double)sigma[l];
-        T[e] = (double)S[(size_t)j * L + l] / (sg * sg);
-    }
-}
-
-cudaError_t launch_prep_t_diag(const float *S, const float *sigma, int L, int P, double *T,
-                               cudaStream_t st)
-{
-    const long long lp = (long long)L * P;
-    const int tb = (int)((lp + 255) / 256 < 1024 ? (lp + 255) / 256 : 1024);
-    prep_t_diag_kernel<<<tb, 256, 0, st>>>(S, sigma, L, P, T);
-    return cudaGetLastError();
-}
-
 // Outputs of the slo / pos constraint sets: the internal problem has the
 // slack as coordinate P (last); user x = M x', sx = M sx' for the first P
 // coordinates; with bound_check (pos), a pixel whose slack is zero reached

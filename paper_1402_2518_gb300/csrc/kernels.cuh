@@ -54,24 +54,27 @@ cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP
 // Full noise covariance: C^-1 (L x L fp64, device), T scratch (L x P fp64).
 cudaError_t launch_prep_cov(const float *S, const double *Cinv, int L, int P, int PP,
                             const Prep &o, double *T, cudaStream_t st);
-// Tensor-core projection (project_tc.cu).  T: W^2 S^T (per band, from
-// launch_prep_t_diag) or C^-1 S^T (full covariance), L x P fp64; mode
-// LINMIN_PROJ_TC or LINMIN_PROJ_BF16; err: bit 2 set when an MMA did not
-// complete within the wait limit.
-cudaError_t launch_prep_t_diag(const float *S, const float *sigma, int L, int P, double *T,
-                               cudaStream_t st);
+// Tensor-core projection (project_tc.cu): mode LINMIN_PROJ_TC or
+// LINMIN_PROJ_BF16; err: bit 2 set when an MMA did not complete within the
+// wait limit.
 size_t tc_bslice_bytes(int L, int P, int mode);
-cudaError_t launch_tc_prep(const double *T, int L, int P, const double *scale, int mode,
-                           __nv_bfloat16 *bsl, int *fexp, cudaStream_t st);
+// B~ column exponents (exact mode) and slices: from T (C^-1 S^T) when T is
+// given, else from S and sigma (T = W^2 S^T formed on the fly); two
+// launches in the exact mode, one in the bf16 mode
+cudaError_t launch_tc_prep(const float *S, const float *sigma, const double *T, int L, int P,
+                           const double *scale, int mode, __nv_bfloat16 *bsl, int *fexp,
+                           cudaStream_t st);
 cudaError_t launch_project_tc(const float *cube, long long N, int L, int P, int mode,
                               const __nv_bfloat16 *bsl, const int *fexp, float *c_hi,
                               float *c_lo, int *err, cudaStream_t st);
-// TMA-fed exact projection (per-pixel exponent pass into rexp, N ints,
-// then the warp-specialised GEMM): usable when rows are 16-byte strided and
-// aligned; otherwise launch_project_tc.
+// TMA-fed exact projection: launch_rowexp writes the per-pixel exponents
+// (rexp, N ints), then launch_project_tma runs the warp-specialised GEMM
+// that reads them; usable when rows are 16-byte strided and aligned,
+// otherwise launch_project_tc.
 bool tma_projection_usable(const float *cube, long long N, int L);
+cudaError_t launch_rowexp(const float *cube, long long N, int L, int *rexp, cudaStream_t st);
 cudaError_t launch_project_tma(const float *cube, long long N, int L, int P,
-                               const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
+                               const __nv_bfloat16 *bsl, const int *fexp, const int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st);
 // slo / pos outputs from the slack-augmented internal problem
 // Per-pixel column subsets (the second pass of Sec. 5): for pixel n and

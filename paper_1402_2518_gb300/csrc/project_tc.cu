@@ -154,30 +154,50 @@ template <> struct TcMode<LINMIN_PROJ_BF16> { static constexpr int NS = 1, NL = 
 }  // namespace
 
 // ---------------------------------------------------------------- B~ slices
-// Column exponents f_j: max_l |B~_lj| < 2^f_j (exact mode).  Warp per column.
-__global__ void tc_bexp_kernel(const double *__restrict__ T, int L, int P,
-                               const double *__restrict__ scale, int *__restrict__ fexp)
+// B~ = T / s with T = W^2 S^T (T_lj = S_jl / sigma_l^2, formed here from S
+// and sigma) or T = C^-1 S^T (given, L x P).
+__device__ __forceinline__ double tc_T(const float *__restrict__ S, const float *__restrict__ sigma,
+                                       const double *__restrict__ Tin, int L, int P, int l, int j)
 {
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (j >= P) return;
+    if (Tin) return Tin[(size_t)l * P + j];
+    const double sg = (double)sigma[l];
+    return (double)S[(size_t)j * L + l] / (sg * sg);
+}
+
+// Column exponents f_j: max_l |B~_lj| < 2^f_j (exact mode).  Block per
+// column, a band per thread (the fp64 divisions of a column in parallel).
+constexpr int BEXP_THREADS = 256;
+
+__global__ void __launch_bounds__(BEXP_THREADS)
+tc_bexp_kernel(const float *__restrict__ S, const float *__restrict__ sigma,
+               const double *__restrict__ Tin, int L, int P, const double *__restrict__ scale,
+               int *__restrict__ fexp)
+{
+    __shared__ double wmax[BEXP_THREADS / 32];
+    const int j = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double s = scale[0];
     double m = 0.0;
-    for (int l = lane; l < L; l += 32) m = fmax(m, fabs(T[(size_t)l * P + j] / s));
+    for (int l = threadIdx.x; l < L; l += BEXP_THREADS)
+        m = fmax(m, fabs(tc_T(S, sigma, Tin, L, P, l, j) / s));
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) {
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < BEXP_THREADS / 32; ++w) m = fmax(m, wmax[w]);
         int e = 0;
         if (m > 0.0) { frexp(m, &e); ++e; }          // |B~_lj| 2^-f_j < 1/2
         fexp[j] = e;
     }
 }
 
-// Slices of B~ = T / s, per 32-band chunk one K-major matrix of NS * NPAD
-// rows (slice q, column j at row q NPAD + j) and 32 bands, in the MMA's
-// canonical layout: an MMA with B = rows [0, (NS - i) NPAD) pairs A slice i
-// with every B slice q <= NS - 1 - i at once, and a 64-band chunk is two
-// consecutive blocks.  Rows j >= P and bands l >= L are zero.
+// Slices per 32-band block: one K-major matrix of NS * NPAD rows (slice q,
+// column j at row q NPAD + j) and 32 bands, in the MMA's canonical layout:
+// an MMA with B = rows [0, (NS - i) NPAD) pairs A slice i with every B slice
+// q <= NS - 1 - i at once, and a 64-band chunk is two consecutive blocks.
+// Rows j >= P and bands l >= L are zero.
 template <int MODE>
-__global__ void tc_bslice_kernel(const double *__restrict__ T, int L, int P, int NPAD,
+__global__ void tc_bslice_kernel(const float *__restrict__ S, const float *__restrict__ sigma,
+                                 const double *__restrict__ Tin, int L, int P, int NPAD,
                                  const double *__restrict__ scale, const int *__restrict__ fexp,
                                  __nv_bfloat16 *__restrict__ out, int nblocks)
 {
@@ -191,7 +211,7 @@ __global__ void tc_bslice_kernel(const double *__restrict__ T, int L, int P, int
         const int rem = (int)(e % (NPAD * KB));
         const int j = rem / KB, k = rem % KB;
         const int l = c * KB + k;
-        const double v = (j < P && l < L) ? T[(size_t)l * P + j] / s : 0.0;
+        const double v = (j < P && l < L) ? tc_T(S, sigma, Tin, L, P, l, j) / s : 0.0;
         char *blk = reinterpret_cast<char *>(out) + (size_t)c * NS * NPAD * KB * 2;
         if (MODE == LINMIN_PROJ_BF16) {
             *reinterpret_cast<__nv_bfloat16 *>(blk + kmaj(j, k, NPAD)) = __double2bfloat16(v);
@@ -440,44 +460,63 @@ project_tc_kernel(const float *__restrict__ cube, long long N, int L, int P,
 }
 
 // --------------------------------------------------- TMA-fed exact GEMM
-// Per-pixel exponents (max_l |y_l| < 2^e) in one coalesced pass: a warp
-// takes 4 consecutive rows, 16-byte loads (this path requires 16-byte
-// strided rows), every load of the 4 rows issued before the reductions.
-constexpr int ROWEXP_ROWS = 4;
+// Per-pixel exponents (max_l |y_l| < 2^e) in one coalesced pass: a
+// half-warp per row (16-byte loads; this path requires 16-byte strided
+// rows), a warp takes 8 consecutive rows per step, every load of a step
+// issued before the reductions; grid-stride over the cube.
+constexpr int ROWEXP_ROWS = 8;
 
 __global__ void tc_rowexp_kernel(const float *__restrict__ cube, long long N, int L,
                                  int *__restrict__ rexp)
 {
-    const long long n0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * ROWEXP_ROWS;
-    const int lane = threadIdx.x & 31;
-    if (n0 >= N) return;
+    const int lane = threadIdx.x & 31, hw = lane >> 4, hl = lane & 15;
     const int L4 = L / 4;
-    float m[ROWEXP_ROWS];
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long n0 = w0 * ROWEXP_ROWS; n0 < N; n0 += nw * ROWEXP_ROWS) {
+        float m[ROWEXP_ROWS / 2];
 #pragma unroll
-    for (int r = 0; r < ROWEXP_ROWS; ++r) m[r] = 0.f;
-    for (int l = lane; l < L4; l += 32) {
-        float4 v[ROWEXP_ROWS];
+        for (int r = 0; r < ROWEXP_ROWS / 2; ++r) m[r] = 0.f;
+        for (int l = hl; l < L4; l += 16) {
+            float4 v[ROWEXP_ROWS / 2];
 #pragma unroll
-        for (int r = 0; r < ROWEXP_ROWS; ++r)
-            v[r] = n0 + r < N ? __ldg(reinterpret_cast<const float4 *>(cube + (size_t)(n0 + r) * L) + l)
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = 0; r < ROWEXP_ROWS / 2; ++r) {
+                const long long n = n0 + 2 * r + hw;
+                v[r] = n < N ? __ldg(reinterpret_cast<const float4 *>(cube + (size_t)n * L) + l)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
 #pragma unroll
-        for (int r = 0; r < ROWEXP_ROWS; ++r)
-            m[r] = fmaxf(fmaxf(m[r], fmaxf(fabsf(v[r].x), fabsf(v[r].y))),
-                         fmaxf(fabsf(v[r].z), fabsf(v[r].w)));
+            for (int r = 0; r < ROWEXP_ROWS / 2; ++r)
+                m[r] = fmaxf(fmaxf(m[r], fmaxf(fabsf(v[r].x), fabsf(v[r].y))),
+                             fmaxf(fabsf(v[r].z), fabsf(v[r].w)));
+        }
+#pragma unroll
+        for (int r = 0; r < ROWEXP_ROWS / 2; ++r)
+            for (int off = 8; off > 0; off >>= 1)
+                m[r] = fmaxf(m[r], __shfl_xor_sync(0xffffffffu, m[r], off));
+        if (hl < ROWEXP_ROWS / 2) {
+            float mm = m[0];
+#pragma unroll
+            for (int r = 1; r < ROWEXP_ROWS / 2; ++r) mm = hl == r ? m[r] : mm;
+            const long long n = n0 + 2 * hl + hw;
+            int e = 0;
+            if (mm > 0.f) { frexpf(mm, &e); ++e; }   // |y_l| 2^-e < 1/2
+            if (n < N) rexp[n] = e;
+        }
     }
-#pragma unroll
-    for (int r = 0; r < ROWEXP_ROWS; ++r)
-        for (int off = 16; off > 0; off >>= 1)
-            m[r] = fmaxf(m[r], __shfl_xor_sync(0xffffffffu, m[r], off));
-    if (lane < ROWEXP_ROWS && n0 + lane < N) {
-        float mm = m[0];
-#pragma unroll
-        for (int r = 1; r < ROWEXP_ROWS; ++r) mm = lane == r ? m[r] : mm;
-        int e = 0;
-        if (mm > 0.f) { frexpf(mm, &e); ++e; }       // |y_l| 2^-e < 1/2
-        rexp[n0 + lane] = e;
-    }
+}
+
+cudaError_t launch_rowexp(const float *cube, long long N, int L, int *rexp, cudaStream_t st)
+{
+    if (N <= 0) return cudaSuccess;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long warps = (N + ROWEXP_ROWS - 1) / ROWEXP_ROWS;
+    const long long blocks = (warps * 32 + 255) / 256;
+    tc_rowexp_kernel<<<(unsigned)(blocks < 8LL * sms ? blocks : 8LL * sms), 256, 0, st>>>(cube, N, L,
+                                                                                         rexp);
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
@@ -1112,7 +1151,7 @@ bool tma_projection_usable(const float *cube, long long N, int L)
 
 template <int NPAD>
 static cudaError_t launch_ws_t(const float *cube, long long N, int L, int P,
-                               const __nv_bfloat16 *bsl, const int *fexp, int *rexp,
+                               const __nv_bfloat16 *bsl, const int *fexp, const int *rexp,
                                float *c_hi, float *c_lo, int *err, cudaStream_t st)
 {
     CUtensorMap map;
@@ -1129,8 +1168,6 @@ static cudaError_t launch_ws_t(const float *cube, long long N, int L, int P,
     cudaError_t e = cudaFuncSetAttribute(project_ws_kernel<NPAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const long long rwarps = (N + ROWEXP_ROWS - 1) / ROWEXP_ROWS;
-    tc_rowexp_kernel<<<(unsigned)((rwarps * 32 + 255) / 256), 256, 0, st>>>(cube, N, L, rexp);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1142,7 +1179,7 @@ static cudaError_t launch_ws_t(const float *cube, long long N, int L, int P,
 }
 
 cudaError_t launch_project_tma(const float *cube, long long N, int L, int P,
-                               const __nv_bfloat16 *bsl, const int *fexp, int *rexp, float *c_hi,
+                               const __nv_bfloat16 *bsl, const int *fexp, const int *rexp, float *c_hi,
                                float *c_lo, int *err, cudaStream_t st)
 {
     if (N <= 0) return cudaSuccess;
@@ -1164,21 +1201,22 @@ size_t tc_bslice_bytes(int L, int P, int mode)
     return (size_t)nchunks * NS * NPAD * TC_KC * 2;
 }
 
-cudaError_t launch_tc_prep(const double *T, int L, int P, const double *scale, int mode,
-                           __nv_bfloat16 *bsl, int *fexp, cudaStream_t st)
+cudaError_t launch_tc_prep(const float *S, const float *sigma, const double *T, int L, int P,
+                           const double *scale, int mode, __nv_bfloat16 *bsl, int *fexp,
+                           cudaStream_t st)
 {
     const int NPAD = ((P + 15) / 16) * 16;
-    const int nchunks = (L + TC_KC - 1) / TC_KC;
+    const int nblocks = 2 * ((L + TC_KC - 1) / TC_KC);
     if (mode == LINMIN_PROJ_TC)
-        tc_bexp_kernel<<<(P * 32 + 255) / 256, 256, 0, st>>>(T, L, P, scale, fexp);
-    const long long total = (long long)nchunks * NPAD * TC_KC;
+        tc_bexp_kernel<<<P, BEXP_THREADS, 0, st>>>(S, sigma, T, L, P, scale, fexp);
+    const long long total = (long long)nblocks * NPAD * (TC_KC / 2);
     const int blocks = (int)((total + 255) / 256 < 1024 ? (total + 255) / 256 : 1024);
     if (mode == LINMIN_PROJ_TC)
-        tc_bslice_kernel<LINMIN_PROJ_TC><<<blocks, 256, 0, st>>>(T, L, P, NPAD, scale, fexp, bsl,
-                                                                 2 * nchunks);
+        tc_bslice_kernel<LINMIN_PROJ_TC><<<blocks, 256, 0, st>>>(S, sigma, T, L, P, NPAD, scale,
+                                                                 fexp, bsl, nblocks);
     else
-        tc_bslice_kernel<LINMIN_PROJ_BF16><<<blocks, 256, 0, st>>>(T, L, P, NPAD, scale, fexp,
-                                                                   bsl, 2 * nchunks);
+        tc_bslice_kernel<LINMIN_PROJ_BF16><<<blocks, 256, 0, st>>>(S, sigma, T, L, P, NPAD, scale,
+                                                                   fexp, bsl, nblocks);
     return cudaGetLastError();
 }
 

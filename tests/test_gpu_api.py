@@ -33,13 +33,13 @@ def test_phase_ring_and_launch_count():
         pkg.linmin_phase_times_at(h, 3)            # only three calls so far
     with pytest.raises(linmin.LinminError):
         pkg.linmin_phase_times_at(h, linmin.LINMIN_PHASE_RING)
-    # prep 3, projection (tensor cores: W^2 S^T, B~ exponents and slices, pixel
+    # prep 3, projection (tensor cores: B~ exponents and slices, pixel
     # exponents, GEMM),
     # IPM, crossover (support, scan, scatter, pass 0, lane groups), retry
     # (2 IPM, support, lane groups), rms
-    assert pkg.linmin_last_launches(h) == 3 + 5 + 1 + 5 + 2 + 2 + 1
+    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 5 + 2 + 2 + 1
     assert pkg.linmin_unmix(h, X, cube.N, sg, x) == 0          # no RMS requested
-    assert pkg.linmin_last_launches(h) == 3 + 5 + 1 + 5 + 2 + 2
+    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 5 + 2 + 2
     assert pkg.linmin_unmix(h, X, 0, sg, x) == 0
     assert pkg.linmin_last_launches(h) == 0
     st, _ = um.wait()
