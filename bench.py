@@ -51,6 +51,19 @@ IPM_TRAFFIC = {"ipm_sha256_12": "a8ebf479dc4e",
 DETECT_TRAFFIC = {"sha256_12": "e16e392227f9", "bytes_per_pixel": 19.948544e6 / 65536}
 
 
+def projection_roofline(n_pix: int, L: int, P: int, phase_ms: float, hbm_gbs: float):
+    """The projection phase against HBM: algorithmic bytes = the cube read
+    once (4 L per pixel) + c~ written (hi and lo words, 8 P per pixel)."""
+    nbytes = n_pix * (4 * L + 8 * P)
+    achieved = nbytes / (phase_ms / 1e3) / 1e9
+    return {"bound": "hbm", "phase_ms": phase_ms, "algorithmic_bytes": nbytes,
+            "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+            "note": "phase = B~ column exponents and slices, the join with the per-pixel "
+                    "exponent pass (a second read of the cube, on a side stream, "
+                    "overlapping the library preparation) and the warp-specialised "
+                    "tensor-core GEMM; peak = measured copy bandwidth"}
+
+
 def detect_traffic(n_pix: int):
     import hashlib
     src = os.path.join(ROOT, "paper_1402_2518_gb300", "csrc", "detect.cu")
@@ -808,6 +821,8 @@ def main():
                                     "the fraction is slightly conservative",
                      "flops_per_iter": flop_per_iter,
                      "mean_iters": float(iters.mean().item())},
+        "projection": projection_roofline(N, L, P, phase_tot["project"] / args.steps,
+                                          float(peaks.get("hbm_gbs", 6800.0))),
         "accuracy": acc,
         "phase_ms": {k: v / args.steps for k, v in phase_tot.items()},
         "not_converged": nbad,
