@@ -443,6 +443,30 @@ __global__ void bucket_scatter_kernel(long long N, const int *__restrict__ ksize
     list[pos] = n;
 }
 
+// The same counting sort for a list of pixels (the supports they have now):
+// the lane groups of a warp then start their pixels with similar sizes.
+__global__ void list_hist_kernel(const long long *__restrict__ list,
+                                 const unsigned long long *__restrict__ len,
+                                 const unsigned long long *__restrict__ mask,
+                                 int *__restrict__ ksize, unsigned int *__restrict__ hist)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)*len) return;
+    const int k = __popcll(mask[list[i]]);
+    ksize[i] = k;
+    atomicAdd(hist + k, 1u);
+}
+__global__ void list_scatter_kernel(const long long *__restrict__ list,
+                                    const unsigned long long *__restrict__ len,
+                                    const int *__restrict__ ksize,
+                                    unsigned long long *__restrict__ cursor,
+                                    long long *__restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)*len) return;
+    out[atomicAdd(cursor + ksize[i], 1ULL)] = list[i];
+}
+
 // One pass of the active-set crossover.  For each listed pixel, solve the
 // equality-constrained problem on its support S (mask) in fp64 through the
 // Cholesky factor of G~_SS (positive definite since rank [S^T; 1^T] = P),
@@ -696,11 +720,13 @@ constexpr int XG = 8;
 template <int KMAX>
 struct XGCfg {
     static constexpr int KS = (KMAX + XG - 1) / XG;        // row slots per lane
-    static constexpr int LSZ = KMAX * (KMAX + 1) / 2;      // packed lower triangle
     static constexpr int THREADS = KMAX > 48 ? 32 : 64;    // 4 or 8 groups per block
     static constexpr int GROUPS = THREADS / XG;
-    static constexpr int GROUP_WORDS = 2 * LSZ + 3 * KMAX; // L hi/lo, x hi/lo, support list
-    static size_t smem(int P) { return sizeof(float) * (2 * (size_t)P * P + (size_t)GROUPS * GROUP_WORDS); }
+    // per group, sized by P (supports have at most P coordinates, so the
+    // occupancy follows the library rather than the bucket): L hi/lo as
+    // packed lower triangles, x hi/lo, the support list
+    static int group_words(int P) { return P * (P + 1) + 3 * P; }
+    static size_t smem(int P) { return sizeof(float) * (2 * (size_t)P * P + (size_t)GROUPS * group_words(P)); }
 };
 
 __device__ __forceinline__ int pk(int r, int c) { return r * (r + 1) / 2 + c; }
@@ -745,9 +771,10 @@ crossover_group_kernel(const CrossArgs a)
     }
     const int lane = threadIdx.x & 31, t = lane % XG, grp = threadIdx.x / XG;
     const unsigned gmask = ((1u << XG) - 1u) << ((lane / XG) * XG);
-    float *Lh = sgm + 2 * P * P + (size_t)grp * C::GROUP_WORDS;
-    float *Ll = Lh + C::LSZ, *xh = Ll + C::LSZ, *xl = xh + KMAX;
-    int *sidx = reinterpret_cast<int *>(xl + KMAX);
+    const int lsz = P * (P + 1) / 2;
+    float *Lh = sgm + 2 * P * P + (size_t)grp * (2 * lsz + 3 * P);
+    float *Ll = Lh + lsz, *xh = Ll + lsz, *xl = xh + P;
+    int *sidx = reinterpret_cast<int *>(xl + P);
     __syncthreads();
     const df zero = df_make(0.f);
     const long long stride = (long long)gridDim.x * C::GROUPS;
@@ -761,13 +788,15 @@ crossover_group_kernel(const CrossArgs a)
         for (int solve = 0;; ++solve) {
             const bool can_flip = solve + 1 < a.max_solves;
             const int k = __popcll(m);
+            // row slots in use: the slot loops (unrolled to KS) stop there
+            const int ks = (k + XG - 1) / XG;
             for (int i = t; i < P; i += XG)
                 if ((m >> i) & 1ULL) sidx[__popcll(m & ((1ULL << i) - 1ULL))] = i;
             __syncwarp(gmask);
             // L = G~_SS on the own rows; right-hand sides 1 and c~_S
             df au[KS], av[KS], uu[KS], vv[KS];
 #pragma unroll
-            for (int s = 0; s < KS; ++s) {
+            for (int s = 0; s < KS && s < ks; ++s) {
                 const int r = s * XG + t;
                 au[s] = av[s] = uu[s] = vv[s] = zero;
                 if (r < k) {
@@ -790,7 +819,7 @@ crossover_group_kernel(const CrossArgs a)
                 const df rl = df_rsqrt(d);
                 df uc = zero, vc = zero, lrc[KS];
 #pragma unroll
-                for (int s = 0; s < KS; ++s) {
+                for (int s = 0; s < KS && s < ks; ++s) {
                     const int r = s * XG + t;
                     lrc[s] = zero;
                     if (r > c && r < k) {
@@ -811,7 +840,7 @@ crossover_group_kernel(const CrossArgs a)
                 vc = shfl_df(gmask, vc, c % XG);
                 __syncwarp(gmask);                       // column c of L stored
 #pragma unroll
-                for (int s = 0; s < KS; ++s) {
+                for (int s = 0; s < KS && s < ks; ++s) {
                     const int r = s * XG + t;
                     if (r > c && r < k) {
                         au[s] = df_fms(au[s], lrc[s], uc);
@@ -823,7 +852,7 @@ crossover_group_kernel(const CrossArgs a)
                 for (int j = c + 1; j < k; ++j) {
                     const df ljc = df{Lh[pk(j, c)], Ll[pk(j, c)]};
 #pragma unroll
-                    for (int s = 0; s < KS; ++s) {
+                    for (int s = 0; s < KS && s < ks; ++s) {
                         const int r = s * XG + t;
                         if (r >= j && r < k) {
                             const df v = df_fms(df{Lh[pk(r, j)], Ll[pk(r, j)]}, lrc[s], ljc);
@@ -837,7 +866,7 @@ crossover_group_kernel(const CrossArgs a)
             // nu from the bordered system
             df a11 = zero, a1b = zero;
 #pragma unroll
-            for (int s = 0; s < KS; ++s)
+            for (int s = 0; s < KS && s < ks; ++s)
                 if (s * XG + t < k) {
                     a11 = df_add(a11, df_mul(uu[s], uu[s]));
                     a1b = df_add(a1b, df_mul(uu[s], vv[s]));
@@ -848,7 +877,7 @@ crossover_group_kernel(const CrossArgs a)
             // back solve: xs = L^-T (v - nu u), ub = L^-T u (= G~_SS^-1 1)
             df ax[KS], ab[KS], xs[KS], ub[KS];
 #pragma unroll
-            for (int s = 0; s < KS; ++s) {
+            for (int s = 0; s < KS && s < ks; ++s) {
                 ax[s] = df_fms(vv[s], nu, uu[s]);
                 ab[s] = uu[s];
                 xs[s] = ub[s] = zero;
@@ -856,7 +885,7 @@ crossover_group_kernel(const CrossArgs a)
             for (int r = k - 1; r >= 0; --r) {
                 df xr = zero, ur = zero;
 #pragma unroll
-                for (int s = 0; s < KS; ++s)
+                for (int s = 0; s < KS && s < ks; ++s)
                     if (s * XG + t == r) {
                         const df rlr = df{Lh[pk(r, r)], Ll[pk(r, r)]};
                         xr = df_mul(ax[s], rlr);
@@ -867,7 +896,7 @@ crossover_group_kernel(const CrossArgs a)
                 xr = shfl_df(gmask, xr, r % XG);
                 ur = shfl_df(gmask, ur, r % XG);
 #pragma unroll
-                for (int s = 0; s < KS; ++s) {
+                for (int s = 0; s < KS && s < ks; ++s) {
                     const int q = s * XG + t;
                     if (q < r) {
                         const df lrq = df{Lh[pk(r, q)], Ll[pk(r, q)]};
@@ -883,7 +912,7 @@ crossover_group_kernel(const CrossArgs a)
                 float xmin = (float)-a.tol_x;
                 int fr = -1;
 #pragma unroll
-                for (int s = 0; s < KS; ++s) {
+                for (int s = 0; s < KS && s < ks; ++s) {
                     const int r = s * XG + t;
                     if (r < k) {
                         if (xs[s].hi < xmin) { xmin = xs[s].hi; fr = r; }
@@ -896,7 +925,7 @@ crossover_group_kernel(const CrossArgs a)
                 if (flip == -1) {
                     // most negative multiplier off S, coordinates spread over the lanes
 #pragma unroll
-                    for (int s = 0; s < KS; ++s) {
+                    for (int s = 0; s < KS && s < ks; ++s) {
                         const int r = s * XG + t;
                         if (r < k) { xh[r] = xs[s].hi; xl[r] = xs[s].lo; }
                     }
@@ -927,7 +956,7 @@ crossover_group_kernel(const CrossArgs a)
                 for (int i = t; i < P; i += XG)
                     if (!((m >> i) & 1ULL)) a.x_out[base + i] = 0.f;
 #pragma unroll
-                for (int s = 0; s < KS; ++s) {
+                for (int s = 0; s < KS && s < ks; ++s) {
                     const int r = s * XG + t;
                     if (r < k) a.x_out[base + sidx[r]] = xs[s].hi > 0.f ? df_div(xs[s], xsum).hi : 0.f;
                 }
@@ -938,11 +967,11 @@ crossover_group_kernel(const CrossArgs a)
                         const df rlj = df{Lh[pk(j, j)], Ll[pk(j, j)]};
                         df acc[KS];
 #pragma unroll
-                        for (int s = 0; s < KS; ++s) acc[s] = zero;
+                        for (int s = 0; s < KS && s < ks; ++s) acc[s] = zero;
                         for (int q = j + 1; q < k; ++q) {
                             const df lqj = df{Lh[pk(q, j)], Ll[pk(q, j)]};
 #pragma unroll
-                            for (int s = 0; s < KS; ++s) {
+                            for (int s = 0; s < KS && s < ks; ++s) {
                                 const int i = s * XG + t;
                                 if (i >= q && i < k)
                                     acc[s] = df_fms(acc[s], df{Lh[pk(i, q)], Ll[pk(i, q)]}, lqj);
@@ -950,7 +979,7 @@ crossover_group_kernel(const CrossArgs a)
                         }
                         __syncwarp(gmask);               // column j read by every row
 #pragma unroll
-                        for (int s = 0; s < KS; ++s) {
+                        for (int s = 0; s < KS && s < ks; ++s) {
                             const int i = s * XG + t;
                             if (i > j && i < k) {
                                 const df v = df_mul(acc[s], rlj);
@@ -966,10 +995,10 @@ crossover_group_kernel(const CrossArgs a)
                         if (!((m >> i) & 1ULL)) a.sx_out[base + i] = 0.f;
                     df nrm[KS];
 #pragma unroll
-                    for (int s = 0; s < KS; ++s) nrm[s] = zero;
+                    for (int s = 0; s < KS && s < ks; ++s) nrm[s] = zero;
                     for (int i = t; i < k; ++i) {
 #pragma unroll
-                        for (int s = 0; s < KS; ++s) {
+                        for (int s = 0; s < KS && s < ks; ++s) {
                             const int j = s * XG + t;
                             if (j <= i) {
                                 const df w = df{Lh[pk(i, j)], Ll[pk(i, j)]};
@@ -978,7 +1007,7 @@ crossover_group_kernel(const CrossArgs a)
                         }
                     }
 #pragma unroll
-                    for (int s = 0; s < KS; ++s) {
+                    for (int s = 0; s < KS && s < ks; ++s) {
                         const int j = s * XG + t;
                         if (j < k) {
                             const df var = df_sub(nrm[s], df_mul(df_mul(ub[s], ub[s]), inv_a11));
@@ -1090,7 +1119,13 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
         a.len_out = w.len + 1;
         e = launch_pass(a, st);
         if (e != cudaSuccess) return e;
-        a.list_in = w.list[1];
+        // the flipped pixels, sorted by their new support size into list 0
+        e = cudaMemsetAsync(w.hist, 0, sizeof(unsigned int) * (base.P + 1), st);
+        if (e != cudaSuccess) return e;
+        list_hist_kernel<<<gridN, T, 0, st>>>(w.list[1], w.len + 1, base.mask, w.ksize, w.hist);
+        bucket_scan_kernel<<<1, 32, 0, st>>>(base.P, w.hist, w.cursor, w.len_all);
+        list_scatter_kernel<<<gridN, T, 0, st>>>(w.list[1], w.len + 1, w.ksize, w.cursor, w.list[0]);
+        a.list_in = w.list[0];
         a.len_in = w.len + 1;
         a.max_solves = MAX_SWAPS;
     } else {

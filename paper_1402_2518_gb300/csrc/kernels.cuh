@@ -47,7 +47,7 @@ struct Prep {
 // them so that the launch count the C ABI reports stays exact)
 constexpr int PREP_LAUNCHES = 3;
 constexpr int PREP_COV_LAUNCHES = 4;
-constexpr int crossover_launches(bool whole_cube) { return whole_cube ? 3 + 2 : 1 + 1; }
+constexpr int crossover_launches(bool whole_cube) { return whole_cube ? 3 + 3 + 2 : 1 + 1; }
 
 cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP,
                         const Prep &o, cudaStream_t st);
