@@ -37,12 +37,12 @@ METRIC = "pixels/s IPLS unmix at <=1e-4 abs err vs FP64 oracle; served p50/p99 l
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes per pixel of the main interior-point launch, from the ncu
-# capture summarised in profiles/ipm_and_projection_omega65k_full.md
+# capture summarised in profiles/ipm_omega65k_full.md
 # (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels; traffic
 # grows with the pixel count).  Valid only for the kernel source it was
 # measured on (hash of csrc/ipm.cuh).
-IPM_TRAFFIC = {"ipm_sha256_12": "a8ebf479dc4e",
-               "bytes_per_pixel": (9.524992e6 + 0.027648e6) / 65536}
+IPM_TRAFFIC = {"ipm_sha256_12": "674da1bbcd7e",
+               "bytes_per_pixel": (9.579776e6 + 0.0064e6) / 65536}
 
 
 # DRAM bytes of detect_kernel (ncu, 65,536 pixels: 19,948,544 read, 0

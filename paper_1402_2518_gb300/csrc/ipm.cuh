@@ -24,12 +24,25 @@
 // Mapping: a group of G consecutive lanes owns one pixel; lane t owns rows
 // i = s*G + t (slot s < NS) of the lower triangle of H, kept in registers
 // (row length (s+1)*G, fully unrolled, compile-time indices).  The
-// right-looking factorisation broadcasts column k through shared memory
-// (all columns are kept: they serve the back solves), the right-hand sides
-// 1 and r_aff are eliminated during the factorisation (forward solves for
-// free).  Groups take pixels from a global work counter and refill as soon
-// as their pixel leaves the active set (converged pixels are compacted out
-// of the running set; warps run while any group has work).
+// factorisation is right-looking and leaves the columns of L in shared
+// memory, where the triangular solves read them; the right-hand sides 1 and
+// r_aff are eliminated during the factorisation (forward solves for free).
+//   * G = 4: by blocks of four columns (one slot).  Every lane of the group
+//     factors the 4 x 4 diagonal block itself (its rows exchanged through
+//     shared memory), forms its own panel rows in place and updates the
+//     trailing rows with a rank-4 update in packed FMAs (fma.rn.f32x2):
+//     every register index is a compile-time constant, so there are no
+//     selects or predicated updates.
+//   * G > 4: column by column, the G columns of a slot sharing one copy of
+//     the code (a rolled loop, the column picked by selects), which keeps
+//     the loop body of the wider groups small.
+// The solves go by blocks of G rows through the inverses of the diagonal
+// blocks of L (stored in place of those blocks): one gather of G values by
+// shuffles per block instead of one broadcast per row, and every shared
+// memory address of the column reads a compile-time offset.  Groups take
+// pixels from a global work counter and refill as soon as their pixel
+// leaves the active set (converged pixels are compacted out of the running
+// set; warps run while any group has work).
 //
 // Two instantiations per size: ACC = false iterates with the float32 KKT
 // residual until mu <= mu_ref and saves the state; ACC = true continues with
@@ -46,6 +59,17 @@ namespace lm {
 // memory loads of later unrolled steps (which would hold them all in
 // registers at once).
 #define LM_STEP_FENCE() asm volatile("" ::: "memory")
+
+
+// two FMAs in one instruction: (d0, d1) = (a0 * b0 + c0, a1 * b1 + c1), operands
+// passed as scalars so that the register arrays stay scalarisable
+LM_DEV void ffma2s(float &d0, float &d1, float a0, float a1, float b0, float b1, float c0, float c1)
+{
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
 
 struct IpmArgs {
     long long N;
@@ -71,12 +95,17 @@ struct IpmCfg {
     static constexpr int NS = NS_, G = G_;
     static constexpr int PP = NS * G;      // padded size, multiple of 4
     static constexpr int GPW = 32 / G;     // pixel groups per warp
-    // registers of H per lane (rows of (s+1)*G floats) and the resident
-    // blocks per SM the register budget is sized for: 2 blocks above 100
-    // registers of H (9x4: 180, 4x16: 160, 5x8: 120), else 3
+    // registers of H per lane (rows of (s+1)*G floats)
     static constexpr int H_REGS = NS * (NS + 1) / 2 * G;
-    static constexpr int MIN_BLOCKS = H_REGS > 100 ? 2 : 3;
-    static constexpr int WARPS = 4;       // warps per block
+    // Warps per block and the resident blocks per SM the register budget is
+    // sized for.  Four-lane groups run the block-panel factorisation, whose
+    // unrolled loop body is large: eight warps per block iterate in
+    // lockstep, so the two warps of each scheduler fetch the same
+    // instructions (one 8-warp block per SM above 100 registers of H, else 2).
+    // Wider groups keep 4-warp blocks (2 per SM above 100 registers of H,
+    // else 3).
+    static constexpr int WARPS = (G == 4) ? 8 : 4;
+    static constexpr int MIN_BLOCKS = (G == 4) ? (H_REGS > 100 ? 1 : 2) : (H_REGS > 100 ? 2 : 3);
     static constexpr int THREADS = WARPS * 32;
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
     static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
@@ -87,10 +116,14 @@ struct IpmCfg {
         const int A = k / 4;
         return k * PP - 4 * (2 * A * (A - 1) + A * (k - 4 * A + 1));
     }
+    // offset of column k's storage such that L[i][k] = buf[coloff(k) + i]
+    static constexpr __host__ __device__ int coloff(int k) { return colstart(k) - alignrow(k); }
     static constexpr int LBUF = colstart(PP);
-    // per-group floats: L columns + x broadcast; stride = 4 (mod 32) words
-    // so that the GPW groups of a warp hit distinct banks with LDS.128
-    static constexpr int GROUP_RAW = LBUF + PP;
+    // per-group floats: L columns + a broadcast area (x in the residual, the
+    // diagonal block rows in the factorisation: at least 32 floats); stride
+    // = 4 (mod 32) words so that the GPW groups of a warp hit distinct banks
+    // with LDS.128
+    static constexpr int GROUP_RAW = LBUF + (PP > 32 ? PP : 32);
     static constexpr int GROUP_FLOATS = ((GROUP_RAW + 31) / 32) * 32 + 4;
     static constexpr size_t smem_bytes(bool acc) {
         return sizeof(float) * ((acc ? 2 : 1) * PP * PP + PP +
@@ -196,7 +229,10 @@ ipm_kernel(const IpmArgs a)
     float rd[NS];
     float rp = 0.f, mu = 0.f, rdmax = 0.f, dec = 0.f;
 
-    // r_d = G~ x - c~ - lambda + nu 1 and the scalar measures (group-uniform)
+    // r_d = G~ x - c~ - lambda + nu 1 and the scalar measures (group-uniform).
+    // G~ x is accumulated column by column in one sequential chain per row:
+    // the pos thresholds sit at the float32 floor, and an even/odd split of
+    // the sum (two packed chains) doubled pos's iteration count.
     auto residual = [&]() {
 #pragma unroll
         for (int s = 0; s < NS; ++s) xbuf[s * G + t] = x[s];
@@ -334,131 +370,268 @@ ipm_kernel(const IpmArgs a)
         // ---- factorise H = L L^T; eliminate rhs B1 = 1, B2 = r_aff = -r_d - lambda
         float B1[NS], B2[NS], dinv[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            B1[s] = valid[s] ? 1.f : 0.f;
-            B2[s] = -rd[s] - lam[s];
-        }
-        // Column k = sk*G + tk: the slot block sk is unrolled (register
-        // indices of H stay compile-time), the G columns of a block share one
-        // copy of the code (rolled loop over tk, column picked by selects).
-        // The loop body is then about 1/G of the fully unrolled one: the
-        // kernel is bound by instruction fetch, not by the extra selects.
+        for (int s = 0; s < NS; ++s) { B1[s] = valid[s] ? 1.f : 0.f; B2[s] = -rd[s] - lam[s]; }
+        const float *lb = colbuf + t;      // L[s*G + t][k] = lb[C::coloff(k) + s*G]
+        if constexpr (G == 4) {
+            // Blocks of G = 4 columns (slot b).  (A) the group's four rows of
+            // the diagonal block and their right-hand sides are exchanged
+            // through shared memory; every lane factors the 4 x 4 block, solves
+            // its right-hand sides and forms its inverse M_b (stored in the
+            // block's strictly lower column slots for the triangular solves;
+            // diag M_b = 1/L_kk stays in dinv).  (B) each lane forms its panel
+            // rows L[i][4b..4b+3] = H[i][4b..4b+3] L_bb^-T in place (register
+            // indices stay compile-time), stores them as columns and
+            // eliminates its right-hand sides.  (E) rank-4 update of the later
+            // blocks: per panel column one LDS.128 per four rows of the
+            // trailing matrix, two packed FMAs per owned row.
+            float *xrow = xbuf + 8 * t;
 #pragma unroll
-        for (int sk = 0; sk < NS; ++sk) {
-#pragma unroll 1
-            for (int tk = 0; tk < G; ++tk) {
-                const int k = sk * G + tk;
-                float hk[NS];
-#pragma unroll
-                for (int s = sk; s < NS; ++s) {
-                    float h = H[s][sk * G];
-#pragma unroll
-                    for (int q = 1; q < G; ++q) h = (tk == q) ? H[s][sk * G + q] : h;
-                    hk[s] = h;
-                }
-                float d = __shfl_sync(FULL, hk[sk], tk, G);
-                d = (d > TINY) ? d : BIGPIV;
-                const float r = rsqrtf(d);
-                float *col = colbuf + C::colstart(k) - C::alignrow(k);
-                float lik[NS];
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    const bool below = (s > sk) || (s == sk && t > tk);
-                    lik[s] = (s >= sk && below) ? hk[s] * r : 0.f;
-                    if (s >= sk && below) col[s * G + t] = lik[s];
-                }
-                float z1 = 0.f, z2 = 0.f;
-                if (t == tk) {
-                    dinv[sk] = r;                 // 1 / L_kk, kept by the row's owner
-                    z1 = B1[sk] * r; z2 = B2[sk] * r;
-                    B1[sk] = z1; B2[sk] = z2;
-                }
+            for (int b = 0; b < NS; ++b) {
+                *reinterpret_cast<float4 *>(xrow) = make_float4(H[b][4 * b], H[b][4 * b + 1], H[b][4 * b + 2], H[b][4 * b + 3]);
+                *reinterpret_cast<float2 *>(xrow + 4) = make_float2(B1[b], B2[b]);
                 __syncwarp();
-                z1 = __shfl_sync(FULL, z1, tk, G);
-                z2 = __shfl_sync(FULL, z2, tk, G);
-                // columns of block sk right of k (runtime test j > k)
+                float A[4][4], rb1[4], rb2[4];
 #pragma unroll
-                for (int j4 = sk * G / 4; j4 < (sk + 1) * G / 4; ++j4) {
-                    const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
-                    const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
+                for (int p = 0; p < 4; ++p) {
+                    const float4 rv = *reinterpret_cast<const float4 *>(xbuf + 8 * p);
+                    const float2 bv = *reinterpret_cast<const float2 *>(xbuf + 8 * p + 4);
+                    A[p][0] = rv.x; A[p][1] = rv.y; A[p][2] = rv.z; A[p][3] = rv.w;
+                    rb1[p] = bv.x; rb2[p] = bv.y;
+                }
+                float dq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float dd = A[q][q];
+#pragma unroll
+                    for (int r = 0; r < q; ++r) dd = fmaf(-A[q][r], A[q][r], dd);
+                    dd = (dd > TINY) ? dd : BIGPIV;
+                    const float rq = rsqrtf(dd);
+                    dq[q] = rq;
+#pragma unroll
+                    for (int p = q + 1; p < 4; ++p) {
+                        float v = A[p][q];
+#pragma unroll
+                        for (int r = 0; r < q; ++r) v = fmaf(-A[p][r], A[q][r], v);
+                        A[p][q] = v * rq;
+                    }
+                }
+                float z1[4], z2[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float u1 = rb1[q], u2 = rb2[q];
+#pragma unroll
+                    for (int r = 0; r < q; ++r) { u1 = fmaf(-A[q][r], z1[r], u1); u2 = fmaf(-A[q][r], z2[r], u2); }
+                    z1[q] = u1 * dq[q]; z2[q] = u2 * dq[q];
+                }
+                // M_b = L_bb^-1 (strictly lower part), column by column
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    float mc[4];
+                    mc[q] = dq[q];
+#pragma unroll
+                    for (int p = q + 1; p < 4; ++p) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int r = q; r < p; ++r) v = fmaf(A[p][r], mc[r], v);
+                        mc[p] = -dq[p] * v;
+                        colbuf[C::coloff(4 * b + q) + 4 * b + p] = mc[p];
+                    }
+                }
+                dinv[b] = t == 0 ? dq[0] : t == 1 ? dq[1] : t == 2 ? dq[2] : dq[3];
+                B1[b] = t == 0 ? z1[0] : t == 1 ? z1[1] : t == 2 ? z1[2] : z1[3];
+                B2[b] = t == 0 ? z2[0] : t == 1 ? z2[1] : t == 2 ? z2[2] : z2[3];
+#pragma unroll
+                for (int s = b + 1; s < NS; ++s) {
+                    float xq[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * j4 + q;
-                        if (j > k) {
+                        float v = H[s][4 * b + q];
 #pragma unroll
-                            for (int s = sk; s < NS; ++s) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
+                        for (int r = 0; r < q; ++r) v = fmaf(-xq[r], A[q][r], v);
+                        xq[q] = v * dq[q];
+                        H[s][4 * b + q] = xq[q];
+                        colbuf[t + C::coloff(4 * b + q) + 4 * s] = xq[q];
+                        ffma2s(B1[s], B2[s], -xq[q], -xq[q], z1[q], z2[q], B1[s], B2[s]);
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float *col = colbuf + C::coloff(4 * b + q);
+#pragma unroll
+                    for (int j4 = b + 1; j4 < NS; ++j4) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
+#pragma unroll
+                        for (int s = j4; s < NS; ++s) {
+                            const float nl = -H[s][4 * b + q];
+                            ffma2s(H[s][4 * j4], H[s][4 * j4 + 1], nl, nl, lv.x, lv.y, H[s][4 * j4], H[s][4 * j4 + 1]);
+                            ffma2s(H[s][4 * j4 + 2], H[s][4 * j4 + 3], nl, nl, lv.z, lv.w, H[s][4 * j4 + 2], H[s][4 * j4 + 3]);
                         }
                     }
                 }
-                // columns of the later blocks (the bulk of the update)
-#pragma unroll
-                for (int j4 = (sk + 1) * G / 4; j4 < PP / 4; ++j4) {
-                    const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
-                    const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = 4 * j4 + q;
-#pragma unroll
-                        for (int s = j / G; s < NS; ++s) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
-                    }
-                }
-#pragma unroll
-                for (int s = sk; s < NS; ++s) {
-                    B1[s] = fmaf(-lik[s], z1, B1[s]);
-                    B2[s] = fmaf(-lik[s], z2, B2[s]);
-                }
             }
-        }
-        __syncwarp();
-
-        // back solve L^T w = v in place (v distributed by rows); uses the
-        // stored columns of L and 1/L_kk on each owner's diagonal
-        auto back_solve = [&](float (&v)[NS]) {
-            int cb[NS];     // column i = s*G + t starts at cb[s] + alignrow(i)
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                const int i = s * G + t;
-                cb[s] = C::colstart(i) - C::alignrow(i);
-            }
-#pragma unroll
-            for (int sk = NS - 1; sk >= 0; --sk) {
-#pragma unroll 1
-                for (int tk = G - 1; tk >= 0; --tk) {
-                    const int k = sk * G + tk;
-                    float lk[NS];
-#pragma unroll
-                    for (int s = 0; s <= sk; ++s) lk[s] = colbuf[cb[s] + k];
-                    float w = 0.f;
-                    if (t == tk) { w = v[sk] * dinv[sk]; v[sk] = w; }
-                    w = __shfl_sync(FULL, w, tk, G);
-#pragma unroll
-                    for (int s = 0; s <= sk; ++s) {
-                        const bool above = (s < sk) || (t < tk);
-                        if (above) v[s] = fmaf(-lk[s], w, v[s]);
-                    }
-                }
-            }
-        };
-        // forward solve L z = b in place, L read from the stored columns
-        auto fwd_solve = [&](float (&b)[NS]) {
+            __syncwarp();
+        } else {
+            // Column k = sk*G + tk: the slot block sk is unrolled (register
+            // indices of H stay compile-time), the G columns of a block share one
+            // copy of the code (rolled loop over tk, column picked by selects).
+            // The loop body is then about 1/G of the fully unrolled one.
 #pragma unroll
             for (int sk = 0; sk < NS; ++sk) {
 #pragma unroll 1
                 for (int tk = 0; tk < G; ++tk) {
                     const int k = sk * G + tk;
-                    const float *col = colbuf + C::colstart(k) - C::alignrow(k);
-                    float lk[NS];
-#pragma unroll
-                    for (int s = sk; s < NS; ++s) lk[s] = col[s * G + t];
-                    float z = 0.f;
-                    if (t == tk) { z = b[sk] * dinv[sk]; b[sk] = z; }
-                    z = __shfl_sync(FULL, z, tk, G);
+                    float hk[NS];
 #pragma unroll
                     for (int s = sk; s < NS; ++s) {
-                        const bool below = (s > sk) || (t > tk);
-                        if (below) b[s] = fmaf(-lk[s], z, b[s]);
+                        float h = H[s][sk * G];
+#pragma unroll
+                        for (int q = 1; q < G; ++q) h = (tk == q) ? H[s][sk * G + q] : h;
+                        hk[s] = h;
+                    }
+                    float d = __shfl_sync(FULL, hk[sk], tk, G);
+                    d = (d > TINY) ? d : BIGPIV;
+                    const float r = rsqrtf(d);
+                    float *col = colbuf + C::colstart(k) - C::alignrow(k);
+                    float lik[NS];
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        const bool below = (s > sk) || (s == sk && t > tk);
+                        lik[s] = (s >= sk && below) ? hk[s] * r : 0.f;
+                        if (s >= sk && below) col[s * G + t] = lik[s];
+                    }
+                    float z1 = 0.f, z2 = 0.f;
+                    if (t == tk) {
+                        dinv[sk] = r;                 // 1 / L_kk, kept by the row's owner
+                        z1 = B1[sk] * r; z2 = B2[sk] * r;
+                        B1[sk] = z1; B2[sk] = z2;
+                    }
+                    __syncwarp();
+                    z1 = __shfl_sync(FULL, z1, tk, G);
+                    z2 = __shfl_sync(FULL, z2, tk, G);
+                    // columns of block sk right of k (runtime test j > k)
+#pragma unroll
+                    for (int j4 = sk * G / 4; j4 < (sk + 1) * G / 4; ++j4) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
+                        const float lc[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int j = 4 * j4 + q;
+                            if (j > k) {
+#pragma unroll
+                                for (int s = sk; s < NS; ++s) H[s][j] = fmaf(-lik[s], lc[q], H[s][j]);
+                            }
+                        }
+                    }
+                    // columns of the later blocks (the bulk of the update)
+                    float nl[NS];
+#pragma unroll
+                    for (int s = sk; s < NS; ++s) nl[s] = -lik[s];
+#pragma unroll
+                    for (int j4 = (sk + 1) * G / 4; j4 < PP / 4; ++j4) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
+#pragma unroll
+                        for (int s = (4 * j4) / G; s < NS; ++s) {
+                            ffma2s(H[s][4 * j4], H[s][4 * j4 + 1], nl[s], nl[s], lv.x, lv.y, H[s][4 * j4], H[s][4 * j4 + 1]);
+                            ffma2s(H[s][4 * j4 + 2], H[s][4 * j4 + 3], nl[s], nl[s], lv.z, lv.w, H[s][4 * j4 + 2], H[s][4 * j4 + 3]);
+                        }
+                    }
+#pragma unroll
+                    for (int s = sk; s < NS; ++s) ffma2s(B1[s], B2[s], nl[s], nl[s], z1, z2, B1[s], B2[s]);
+                }
+            }
+            __syncwarp();
+
+
+            // ---- inverses M_b of the G x G diagonal blocks of L, written over the
+            // blocks' strictly lower entries in the column buffer (the
+            // factorisation is done with them); diag(M_b) = 1/L_kk stays in dinv
+            // with the row's owner.  Lane t forms column t of M_b by forward
+            // substitution; the block's entries are read by the whole group
+            // (broadcast) before any lane writes.
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                float dq[G], m[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) dq[q] = __shfl_sync(FULL, dinv[b], q, G);
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int r = 0; r < q; ++r) acc = fmaf(colbuf[C::coloff(b * G + r) + b * G + q], m[r], acc);
+                    m[q] = (q == t) ? dinv[b] : ((q > t) ? -dq[q] * acc : 0.f);
+                }
+                __syncwarp();
+                float *ct = colbuf + C::coloff(b * G + t) + b * G;
+#pragma unroll
+                for (int q = 1; q < G; ++q)
+                    if (q > t) ct[q] = m[q];
+            }
+            __syncwarp();
+        }
+
+        // forward solve L z = v in place, by blocks of G rows: the block's G
+        // values are gathered by shuffles, multiplied by M_b (row t), then
+        // scattered into the later blocks (their columns of L read at
+        // compile-time offsets, conflict-free)
+        auto fwd_solve = [&](float (&v)[NS]) {
+#pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                float y[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) y[q] = __shfl_sync(FULL, v[b], q, G);
+                float z = dinv[b] * v[b];
+#pragma unroll
+                for (int q = 0; q < G - 1; ++q)
+                    if (q < t) z = fmaf(lb[C::coloff(b * G + q) + b * G], y[q], z);
+                v[b] = z;
+                if (b + 1 < NS) {
+                    float zq[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) zq[q] = __shfl_sync(FULL, z, q, G);
+#pragma unroll
+                    for (int s = b + 1; s < NS; ++s) {
+#pragma unroll
+                        for (int q = 0; q < G; ++q) v[s] = fmaf(-lb[C::coloff(b * G + q) + s * G], zq[q], v[s]);
                     }
                 }
+            }
+        };
+        // back solve L^T w = v in place, by blocks from the last: the dot
+        // products of the block's columns with the solved rows below are
+        // summed over the group (reduce-scatter: lane t receives column t's),
+        // then the block is solved with M_b^T
+        auto back_solve = [&](float (&v)[NS]) {
+#pragma unroll
+            for (int b = NS - 1; b >= 0; --b) {
+                float d[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int s = b + 1; s < NS; ++s) acc = fmaf(lb[C::coloff(b * G + q) + s * G], v[s], acc);
+                    d[q] = acc;
+                }
+#pragma unroll
+                for (int off = G / 2; off >= 1; off >>= 1) {
+                    const bool hi = (t & off) != 0;
+#pragma unroll
+                    for (int i = 0; i < off; ++i) {
+                        const float keep = hi ? d[i + off] : d[i];
+                        const float send = hi ? d[i] : d[i + off];
+                        d[i] = keep + __shfl_xor_sync(FULL, send, off);
+                    }
+                }
+                const float yv = v[b] - d[0];
+                float y[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) y[q] = __shfl_sync(FULL, yv, q, G);
+                float w = dinv[b] * yv;
+                const float *ct = colbuf + C::coloff(b * G + t) + b * G;
+#pragma unroll
+                for (int q = 1; q < G; ++q)
+                    if (q > t) w = fmaf(ct[q], y[q], w);
+                v[b] = w;
             }
         };
 

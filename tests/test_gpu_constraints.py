@@ -78,6 +78,21 @@ def test_omega_shaped(pkg, constraint):
     check(got, ref, S, sigma)
 
 
+@pytest.mark.parametrize("constraint", ["slo", "pos"])
+def test_omega_full_size_converges(pkg, constraint):
+    """Every pixel of the full 262,144-pixel OMEGA-shaped cube converges
+    under slo and pos, and a seeded sample of 512 pixels matches the oracle.
+    The pos thresholds sit at the float32 floor, where even the summation
+    order of the dual residual decides whether a pixel reaches them: this
+    catches a change of rounding that leaves pixels at the iteration cap."""
+    S, sigma, X = omega_rank_full(None)
+    st, nbad, got = run(pkg, S, sigma, X, constraint)
+    assert st == 0 and nbad == 0
+    rows = np.sort(np.random.default_rng(11).choice(X.shape[0], 512, replace=False))
+    ref = oracle.unmix_constraint(S, sigma, X[rows], constraint)
+    check([g[rows] for g in got], ref, S, sigma)
+
+
 def test_rank_and_size_refusals(pkg):
     from paper_1402_2518_gb300 import linmin
     cube = synth.make_cube(synth.OMEGA_262K, n_pix=4)          # flat + slopes: rank S = P - 1
