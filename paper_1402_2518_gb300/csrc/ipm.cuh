@@ -51,6 +51,7 @@
 // minimiser of the exact data rather than of its float32 rounding.
 #pragma once
 #include "common.cuh"
+#include <type_traits>
 
 namespace lm {
 
@@ -70,6 +71,18 @@ LM_DEV void ffma2s(float &d0, float &d1, float a0, float a1, float b0, float b1,
         "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
         : "=f"(d0), "=f"(d1) : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
 }
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = 0 .. N-1
+template <int I, int N, typename F>
+LM_DEV void lm_static_for_impl(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        lm_static_for_impl<I + 1, N>(f);
+    }
+}
+template <int N, typename F>
+LM_DEV void lm_static_for(F &&f) { lm_static_for_impl<0, N>(f); }
 
 struct IpmArgs {
     long long N;
@@ -381,16 +394,21 @@ ipm_kernel(const IpmArgs a)
             // diag M_b = 1/L_kk stays in dinv).  (B) each lane forms its panel
             // rows L[i][4b..4b+3] = H[i][4b..4b+3] L_bb^-T in place (register
             // indices stay compile-time), stores them as columns and
-            // eliminates its right-hand sides.  (E) rank-4 update of the later
+            // eliminates its right-hand sides.  (C) rank-4 update of the later
             // blocks: per panel column one LDS.128 per four rows of the
-            // trailing matrix, two packed FMAs per owned row.
+            // trailing matrix, two packed FMAs per owned row.  The next slot's
+            // columns are updated first and its rows exchanged at once, so
+            // that the next block's factorisation (a short serial chain) can
+            // overlap the rest of this update (lookahead).
             float *xrow = xbuf + 8 * t;
-#pragma unroll
-            for (int b = 0; b < NS; ++b) {
-                *reinterpret_cast<float4 *>(xrow) = make_float4(H[b][4 * b], H[b][4 * b + 1], H[b][4 * b + 2], H[b][4 * b + 3]);
-                *reinterpret_cast<float2 *>(xrow + 4) = make_float2(B1[b], B2[b]);
+            float A[4][4], rb1[4], rb2[4];
+            // exchange of the diagonal block rows of slot bb (after its
+            // trailing updates) and their right-hand sides
+            auto exchange = [&](auto bbc) {
+                constexpr int bb = decltype(bbc)::value;
+                *reinterpret_cast<float4 *>(xrow) = make_float4(H[bb][4 * bb], H[bb][4 * bb + 1], H[bb][4 * bb + 2], H[bb][4 * bb + 3]);
+                *reinterpret_cast<float2 *>(xrow + 4) = make_float2(B1[bb], B2[bb]);
                 __syncwarp();
-                float A[4][4], rb1[4], rb2[4];
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const float4 rv = *reinterpret_cast<const float4 *>(xbuf + 8 * p);
@@ -398,6 +416,10 @@ ipm_kernel(const IpmArgs a)
                     A[p][0] = rv.x; A[p][1] = rv.y; A[p][2] = rv.z; A[p][3] = rv.w;
                     rb1[p] = bv.x; rb2[p] = bv.y;
                 }
+            };
+            exchange(std::integral_constant<int, 0>{});
+            lm_static_for<NS>([&](auto bc) {
+                constexpr int b = decltype(bc)::value;
                 float dq[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -423,7 +445,6 @@ ipm_kernel(const IpmArgs a)
                     for (int r = 0; r < q; ++r) { u1 = fmaf(-A[q][r], z1[r], u1); u2 = fmaf(-A[q][r], z2[r], u2); }
                     z1[q] = u1 * dq[q]; z2[q] = u2 * dq[q];
                 }
-                // M_b = L_bb^-1 (strictly lower part), column by column
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     float mc[4];
@@ -455,21 +476,29 @@ ipm_kernel(const IpmArgs a)
                     }
                 }
                 __syncwarp();
+                // rank-4 update: first the next slot's columns (they feed the
+                // next block's factorisation), then its exchange, then the
+                // rest, which the scheduler can overlap with the next block
+                auto update_cols = [&](int j4) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float *col = colbuf + C::coloff(4 * b + q);
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(colbuf + C::coloff(4 * b + q) + 4 * j4);
 #pragma unroll
-                    for (int j4 = b + 1; j4 < NS; ++j4) {
-                        const float4 lv = *reinterpret_cast<const float4 *>(col + 4 * j4);
-#pragma unroll
-                        for (int s = j4; s < NS; ++s) {
+                        for (int s = 0; s < NS; ++s) {
+                            if (s < j4) continue;
                             const float nl = -H[s][4 * b + q];
                             ffma2s(H[s][4 * j4], H[s][4 * j4 + 1], nl, nl, lv.x, lv.y, H[s][4 * j4], H[s][4 * j4 + 1]);
                             ffma2s(H[s][4 * j4 + 2], H[s][4 * j4 + 3], nl, nl, lv.z, lv.w, H[s][4 * j4 + 2], H[s][4 * j4 + 3]);
                         }
                     }
+                };
+                if constexpr (b + 1 < NS) {
+                    update_cols(b + 1);
+                    exchange(std::integral_constant<int, b + 1>{});
+#pragma unroll
+                    for (int j4 = b + 2; j4 < NS; ++j4) update_cols(j4);
                 }
-            }
+            });
             __syncwarp();
         } else {
             // Column k = sk*G + tk: the slot block sk is unrolled (register
