@@ -192,6 +192,32 @@ LINMIN_API linmin_status linmin_unmix_cov(linmin_handle h, const float *cube, lo
                                           float *uncertainties, float *residual_rms,
                                           int *iterations);
 
+/*
+ * linmin_unmix (Sec. 2.2-2.3: the same whitening, interior point,
+ * crossover, uncertainties and RMS) of n cubes of uneven sizes in one
+ * queue: every cube's library preparation and projection, then ONE
+ * float32 interior-point launch per group of cubes with the same P and
+ * kernel bucket (a persistent grid, one work counter over all pixels of
+ * the group, each pixel group reading its own cube's G~ through L1), then
+ * every cube's crossover, retry and RMS.
+ *   handles  n handles (distinct; sum-to-one; same device and the same
+ *            cuda_stream, on which everything is queued);
+ *   cubes[i] N[i] x L_i float32, sigmas[i] L_i float32 > 0,
+ *   abundances[i] N[i] x P_i (required); uncertainties, residual_rms,
+ *   iterations: arrays of n pointers or NULL, entries may be NULL;
+ *   every buffer in device memory (LINMIN_ERR_INVALID otherwise).
+ * Results equal those of linmin_unmix on each cube.  Returns after
+ * queueing; linmin_wait(handles[i]) reports cube i's non-converged pixels.
+ * handles[0] keeps the group descriptors on the device.
+ */
+LINMIN_API linmin_status linmin_unmix_batch(int n, const linmin_handle *handles,
+                                            const float *const *cubes, const long long *N,
+                                            const float *const *sigmas,
+                                            float *const *abundances,
+                                            float *const *uncertainties,
+                                            float *const *residual_rms,
+                                            int *const *iterations);
+
 /* Synchronise the handle's stream.  *n_not_converged (may be NULL) receives
  * the number of pixels of the last linmin_unmix that hit max_iter.  Returns
  * LINMIN_ERR_NOT_CONVERGED when that number is non-zero. */

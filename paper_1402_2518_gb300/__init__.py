@@ -6,7 +6,7 @@ from ``csrc/``; ``linmin`` is its ctypes binding.
 from .linmin import (EXPORTED, LinminError, Server, Unmixer, library_path, linmin_create,  # noqa: F401
                      linmin_default_options, linmin_destroy, linmin_last_error,
                      linmin_options, linmin_phase_times, linmin_phase_times_at, linmin_unmix,
-                     linmin_unmix_cov, linmin_unmix_noalloc, linmin_noalloc_scratch_bytes, linmin_fp32_peak, linmin_live_allocations,
+                     linmin_unmix_cov, linmin_unmix_batch, linmin_unmix_noalloc, linmin_noalloc_scratch_bytes, linmin_fp32_peak, linmin_live_allocations,
                      linmin_autotune, linmin_get_lanes, linmin_last_launches, linmin_set_lanes,
                      linmin_version,
                      linmin_server_create, linmin_server_default_options,

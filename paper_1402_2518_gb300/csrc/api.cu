@@ -88,6 +88,18 @@ struct linmin_ctx {
     // only the cube, so it runs while the library is prepared)
     cudaStream_t xstream = nullptr;
     cudaEvent_t xev[2] = {};
+    // linmin_unmix_batch: the call stops after the projection (defer_ipm)
+    // and keeps what the rest of it needs; batch descriptors on the device
+    bool defer_ipm = false;
+    struct {
+        long long N = 0;
+        const float *cube = nullptr;
+        float *x = nullptr, *sx = nullptr, *rms = nullptr;
+        int *it = nullptr;
+        int launches = 0;
+    } pend;
+    unsigned char *bdesc = nullptr;
+    size_t bdesc_cap = 0;
 };
 
 static void mark(linmin_ctx *h, int i)
@@ -491,6 +503,42 @@ static linmin_status ensure_side_stream(linmin_ctx *h)
     return LINMIN_OK;
 }
 
+#define LM_TRY(call) do { const cudaError_t e_ = (call); if (e_ != cudaSuccess) return e_; } while (0)
+// Steps 4 and 5 of a call, after the interior point over all pixels: the
+// crossover of every pixel (failures to the retry list), the retry list
+// through the interior point from the start (float32, then double-float
+// residual) and the crossover again.  Returns the first CUDA error.
+static cudaError_t crossover_and_retry(linmin_ctx *h, long long N, float *d_x, float *d_sx)
+{
+    cudaStream_t st = h->stream;
+    const int P = h->P;
+    IpmArgs ia = ipm_args(h, N);
+    // 4. crossover; failures appended to the retry list
+    CrossArgs ca{};
+    ca.N = N; ca.P = P; ca.Gt64 = h->prep.Gt64; ca.Ghi = h->prep.Ghi; ca.Glo = h->prep.Glo;
+    ca.PP = h->bucket.PP; ca.scale = h->prep.scale; ca.gdiag = h->prep.gdiag;
+    ca.c_hi = h->c_hi; ca.c_lo = h->c_lo; ca.x_in = h->x; ca.lam_in = h->lam;
+    ca.x_out = d_x; ca.sx_out = d_sx; ca.mask = h->mask;
+    ca.retry_list = h->retry; ca.retry_len = h->dcnt + 5; ca.n_unverified = nullptr;
+    ca.tol_x = 1e-9 / h->slack_scale; ca.tol_g = 1e-9 / h->slack_scale;
+    LM_TRY(launch_crossover(ca, h->xw, nullptr, nullptr, st));
+    mark(h, 4);
+    // 5. retry list: the interior point from the start with the accurate
+    //    residual phase, then the crossover again
+    ia.list = h->retry; ia.list_len = h->dcnt + 5;
+    ia.mu_ref = h->opt.refine_mu / (h->slack_scale * h->slack_scale); ia.counter = h->dcnt + 1;
+    LM_TRY(launch_ipm(h->bucket, false, ia, st));
+    ia.counter = h->dcnt + 4;
+    LM_TRY(launch_ipm(h->bucket, true, ia, st));
+    // a pixel the retry crossover cannot verify keeps its interior-point
+    // iterate and is reported as not converged (negative iteration count)
+    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = h->dcnt + 2;
+    ca.it_mark = h->it;
+    LM_TRY(launch_crossover(ca, h->xw, h->retry, h->dcnt + 5, st));
+    mark(h, 5);
+    return cudaSuccess;
+}
+
 static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N, const float *sigma,
                                 const double *cov_inv, float *abundances, float *uncertainties,
                                 float *residual_rms, int *iterations,
@@ -630,35 +678,20 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
         ++proj_launches;
     }
     mark(h, 2);
+    if (h->defer_ipm) {
+        // batch: the interior point of this cube runs in the batch's launch
+        h->pend.N = N; h->pend.cube = d_cube; h->pend.x = d_x; h->pend.sx = d_sx;
+        h->pend.rms = d_rms; h->pend.it = d_it;
+        h->pend.launches = (cov_inv ? PREP_COV_LAUNCHES : PREP_LAUNCHES) + proj_launches;
+        return LINMIN_OK;
+    }
 
     IpmArgs ia = ipm_args(h, N);
     // 3. all pixels: float32 residual until mu <= mu_stop
     ia.counter = h->dcnt + 0;
     LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "interior-point kernel");
     mark(h, 3);
-    // 4. crossover; failures appended to the retry list
-    CrossArgs ca{};
-    ca.N = N; ca.P = P; ca.Gt64 = h->prep.Gt64; ca.Ghi = h->prep.Ghi; ca.Glo = h->prep.Glo;
-    ca.PP = h->bucket.PP; ca.scale = h->prep.scale; ca.gdiag = h->prep.gdiag;
-    ca.c_hi = h->c_hi; ca.c_lo = h->c_lo; ca.x_in = h->x; ca.lam_in = h->lam;
-    ca.x_out = d_x; ca.sx_out = d_sx; ca.mask = h->mask;
-    ca.retry_list = h->retry; ca.retry_len = h->dcnt + 5; ca.n_unverified = nullptr;
-    ca.tol_x = 1e-9 / h->slack_scale; ca.tol_g = 1e-9 / h->slack_scale;
-    LM_CUDA(h, launch_crossover(ca, h->xw, nullptr, nullptr, st), "crossover kernels");
-    mark(h, 4);
-    // 5. retry list: the interior point from the start with the accurate
-    //    residual phase, then the crossover again
-    ia.list = h->retry; ia.list_len = h->dcnt + 5;
-    ia.mu_ref = h->opt.refine_mu / (h->slack_scale * h->slack_scale); ia.counter = h->dcnt + 1;
-    LM_CUDA(h, launch_ipm(h->bucket, false, ia, st), "retry interior-point kernel (float32)");
-    ia.counter = h->dcnt + 4;
-    LM_CUDA(h, launch_ipm(h->bucket, true, ia, st), "retry interior-point kernel (double-float)");
-    // a pixel the retry crossover cannot verify keeps its interior-point
-    // iterate and is reported as not converged (negative iteration count)
-    ca.retry_list = nullptr; ca.retry_len = nullptr; ca.n_unverified = h->dcnt + 2;
-    ca.it_mark = h->it;
-    LM_CUDA(h, launch_crossover(ca, h->xw, h->retry, h->dcnt + 5, st), "retry crossover kernels");
-    mark(h, 5);
+    LM_CUDA(h, crossover_and_retry(h, N, d_x, d_sx), "crossover");
     // host x and sigma_x: final here without a slack; copied back on the
     // copy stream while the RMS runs
     const bool early_out = piped && !h->slack;
@@ -773,6 +806,143 @@ linmin_status linmin_phase_times_at(linmin_handle h, int back, float *ms_out, in
         float ms = 0.f;
         LM_CUDA(h, cudaEventElapsedTime(&ms, set[i], set[i + 1]), "event time");
         ms_out[i] = ms;
+    }
+    return LINMIN_OK;
+}
+
+// The rest of a call stopped by defer_ipm, after the batch's interior
+// point: crossover, retry, RMS and the iteration counts (device buffers,
+// sum-to-one).
+static linmin_status unmix_back(linmin_ctx *h)
+{
+    const long long N = h->pend.N;
+    cudaStream_t st = h->stream;
+    mark(h, 3);
+    LM_CUDA(h, crossover_and_retry(h, N, h->pend.x, h->pend.sx), "crossover");
+    if (h->pend.rms)
+        LM_CUDA(h, launch_rms(h->pend.cube, h->dS, h->pend.x, N, h->L, h->P, h->pend.rms, st),
+                "rms kernel");
+    mark(h, 6);
+    if (h->opt.profile) ++h->calls;
+    // the batch's interior-point launch is counted with the batch, not here
+    h->launches = h->pend.launches + crossover_launches(true) + 2 + crossover_launches(false) +
+                  (h->pend.rms ? 1 : 0);
+    if (h->pend.it)
+        LM_CUDA(h, cudaMemcpyAsync(h->pend.it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
+                "copy iterations");
+    return LINMIN_OK;
+}
+
+linmin_status linmin_unmix_batch(int n, const linmin_handle *handles, const float *const *cubes,
+                                 const long long *N, const float *const *sigmas,
+                                 float *const *abundances, float *const *uncertainties,
+                                 float *const *residual_rms, int *const *iterations)
+{
+    if (n <= 0 || !handles || !handles[0]) return fail(nullptr, LINMIN_ERR_INVALID, "no handles");
+    linmin_ctx *h0 = handles[0];
+    if (!cubes || !N || !sigmas || !abundances)
+        return fail(h0, LINMIN_ERR_INVALID, "cubes, N, sigmas and abundances are required");
+    auto dev_or_null = [](const void *q) { return !q || is_device_ptr(q); };
+    for (int i = 0; i < n; ++i) {
+        linmin_ctx *h = handles[i];
+        if (!h) return fail(h0, LINMIN_ERR_INVALID, "a handle is NULL");
+        if (h->device != h0->device || h->stream != h0->stream)
+            return fail(h0, LINMIN_ERR_INVALID, "batch handles must share the device and the stream");
+        if (h->slack) return fail(h0, LINMIN_ERR_INVALID, "batch handles must be sum-to-one");
+        if (N[i] < 0 || N[i] > (1LL << 40)) return fail(h0, LINMIN_ERR_INVALID, "N out of range");
+        if (N[i] == 0) continue;
+        if (!cubes[i] || !sigmas[i] || !abundances[i])
+            return fail(h0, LINMIN_ERR_INVALID, "cube, sigma and abundances are required");
+        if (!is_device_ptr(cubes[i]) || !is_device_ptr(sigmas[i]) || !is_device_ptr(abundances[i]) ||
+            (uncertainties && !dev_or_null(uncertainties[i])) ||
+            (residual_rms && !dev_or_null(residual_rms[i])) || (iterations && !dev_or_null(iterations[i])))
+            return fail(h0, LINMIN_ERR_INVALID, "batch buffers must be device memory");
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == h && N[j] > 0)
+                return fail(h0, LINMIN_ERR_INVALID, "a handle appears twice in the batch");
+    }
+    cudaStream_t st = h0->stream;
+    LM_CUDA(h0, cudaSetDevice(h0->device), "cudaSetDevice");
+    // 1. every cube up to its projection (library preparation, c~)
+    for (int i = 0; i < n; ++i) {
+        if (N[i] == 0) continue;
+        linmin_ctx *h = handles[i];
+        h->defer_ipm = true;
+        const linmin_status s = unmix_impl(h, cubes[i], N[i], sigmas[i], nullptr, abundances[i],
+                                           uncertainties ? uncertainties[i] : nullptr,
+                                           residual_rms ? residual_rms[i] : nullptr,
+                                           iterations ? iterations[i] : nullptr);
+        h->defer_ipm = false;
+        if (s != LINMIN_OK) {
+            if (h != h0) h0->err = h->err;
+            return s;
+        }
+    }
+    // 2. one interior-point launch per group of cubes with the same bucket,
+    //    P and stopping options: one work counter over all their pixels
+    std::vector<std::vector<int>> groups;
+    for (int i = 0; i < n; ++i) {
+        if (N[i] == 0) continue;
+        const linmin_ctx *h = handles[i];
+        bool placed = false;
+        for (auto &g : groups) {
+            const linmin_ctx *r = handles[g[0]];
+            if (r->bucket.NS == h->bucket.NS && r->bucket.G == h->bucket.G && r->P == h->P &&
+                r->opt.max_iter == h->opt.max_iter && r->opt.tol == h->opt.tol) {
+                g.push_back(i);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) groups.push_back({i});
+    }
+    std::vector<IpmCube> desc;
+    std::vector<size_t> first;
+    for (auto &g : groups) {
+        first.push_back(desc.size());
+        long long start = 0;
+        for (int i : g) {
+            const linmin_ctx *h = handles[i];
+            IpmCube c{};
+            c.N = N[i]; c.start = start; c.c_hi = h->c_hi; c.Ghi = h->prep.Ghi; c.grs = h->prep.grs;
+            c.x_state = h->x; c.lam_state = h->lam; c.nu_state = h->nu; c.it_state = h->it;
+            desc.push_back(c);
+            start += N[i];
+        }
+    }
+    const size_t counters = sizeof(unsigned long long) * groups.size();
+    const size_t need = counters + sizeof(IpmCube) * desc.size();
+    if (need > h0->bdesc_cap) {
+        LM_CUDA(h0, dalloc(h0, &h0->bdesc, need), "batch descriptors");
+        h0->bdesc_cap = need;
+    }
+    if (!groups.empty()) {
+        unsigned long long *cnt = reinterpret_cast<unsigned long long *>(h0->bdesc);
+        IpmCube *ddesc = reinterpret_cast<IpmCube *>(h0->bdesc + counters);
+        LM_CUDA(h0, cudaMemsetAsync(cnt, 0, counters, st), "memset");
+        // pageable source: the copy has taken the data when the call returns
+        LM_CUDA(h0, cudaMemcpyAsync(ddesc, desc.data(), sizeof(IpmCube) * desc.size(),
+                                    cudaMemcpyHostToDevice, st), "copy batch descriptors");
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            linmin_ctx *r = handles[groups[gi][0]];
+            unsigned long long total = 0;
+            for (int i : groups[gi]) total += (unsigned long long)N[i];
+            IpmArgs ia = ipm_args(r, (long long)total);
+            ia.cubes = ddesc + first[gi];
+            ia.n_cubes = (int)groups[gi].size();
+            ia.total = total;
+            ia.counter = cnt + gi;
+            LM_CUDA(h0, launch_ipm_batch(r->bucket, ia, st), "batched interior-point kernel");
+        }
+    }
+    // 3. every cube: crossover, retry, RMS
+    for (int i = 0; i < n; ++i) {
+        if (N[i] == 0) continue;
+        const linmin_status s = unmix_back(handles[i]);
+        if (s != LINMIN_OK) {
+            if (handles[i] != h0) h0->err = handles[i]->err;
+            return s;
+        }
     }
     return LINMIN_OK;
 }
@@ -934,6 +1104,9 @@ linmin_status lm::create_from_host(const float *hS, int L, int P, const linmin_o
         A(dalloc(h, &h->fexp, (size_t)P));
     }
     A(cudaMemcpyAsync(h->dS, hS, (size_t)P * L * 4, cudaMemcpyHostToDevice, h->stream));
+    // linmin_wait before any call reads no flag and no count
+    A(cudaMemsetAsync(h->prep.flags, 0, sizeof(int), h->stream));
+    A(cudaMemsetAsync(h->dcnt, 0, 8 * sizeof(unsigned long long), h->stream));
     A(cudaStreamSynchronize(h->stream));       // hS belongs to the caller
     if (o.profile)
         for (auto &set : h->ev)
@@ -964,7 +1137,7 @@ linmin_status lm::destroy_async(linmin_handle h)
                     h->xw.list[0], h->xw.list[1], h->xw.ksize, h->xw.len, h->xw.len_all,
                     h->xw.cursor, h->xw.hist, h->io_cube, h->io_sigma,
                     h->io_x, h->io_sx, h->io_rms, h->io_it, h->cov, h->covT, h->bsl,
-                    h->fexp, h->xa, h->sxa};
+                    h->fexp, h->xa, h->sxa, h->bdesc};
     for (void *p : ptrs)
         if (p) { cudaFreeAsync(p, h->stream); --g_live_allocs; }
     if (h->cstream) {

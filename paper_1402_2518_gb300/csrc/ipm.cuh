@@ -84,6 +84,17 @@ LM_DEV void lm_static_for_impl(F &&f)
 template <int N, typename F>
 LM_DEV void lm_static_for(F &&f) { lm_static_for_impl<0, N>(f); }
 
+// One cube of a batched launch (sum-to-one handles of the same P): its
+// scaled projection, its G~ and start gradient in global memory, its state
+// arrays, and the first global work index of its pixels.
+struct IpmCube {
+    long long N, start;
+    const float *c_hi;             // N x P
+    const float *Ghi, *grs;        // PP x PP (zero padded), PP
+    float *x_state, *lam_state, *nu_state;
+    int *it_state;
+};
+
 struct IpmArgs {
     long long N;
     int P;
@@ -101,6 +112,12 @@ struct IpmArgs {
     const long long *list;         // optional: pixels to process (else 0..N-1)
     const unsigned long long *list_len;  // number of entries of list
     float mu_ref, tol_c, tol_d, eta;
+    // batched launch (BATCH kernels): one work counter over the pixels of
+    // n_cubes cubes, total = their pixel count; the other per-cube fields
+    // above are unused
+    const IpmCube *cubes = nullptr;
+    int n_cubes = 0;
+    unsigned long long total = 0;
 };
 
 template <int NS_, int G_>
@@ -144,10 +161,11 @@ struct IpmCfg {
     }
 };
 
-template <int NS, int G, bool ACC>
+template <int NS, int G, bool ACC, bool BATCH = false>
 __global__ void __launch_bounds__(IpmCfg<NS, G>::THREADS, IpmCfg<NS, G>::MIN_BLOCKS)
 ipm_kernel(const IpmArgs a)
 {
+    static_assert(!(ACC && BATCH), "batched launches run the float32 phase");
     using C = IpmCfg<NS, G>;
     constexpr int PP = C::PP;
     constexpr unsigned FULL = 0xffffffffu;
@@ -165,12 +183,22 @@ ipm_kernel(const IpmArgs a)
     float *colbuf = grp0 + (warp * C::GPW + gid) * C::GROUP_FLOATS;
     float *xbuf = colbuf + C::LBUF;
 
-    for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
-        sGhi[e] = a.Ghi[e];
-        if (ACC) sGlo[e] = a.Glo[e];
+    if constexpr (!BATCH) {
+        for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
+            sGhi[e] = a.Ghi[e];
+            if (ACC) sGlo[e] = a.Glo[e];
+        }
+        for (int e = threadIdx.x; e < PP; e += blockDim.x) sGrs[e] = a.grs[e];
     }
-    for (int e = threadIdx.x; e < PP; e += blockDim.x) sGrs[e] = a.grs[e];
     __syncthreads();
+    // G~ rows: shared memory, or (batch) the group's current cube in global
+    // memory (read through L1)
+    const float *gG = sGhi;
+    const IpmCube *cb = nullptr;
+    auto ldG4 = [&](const float *q) -> float4 {
+        if constexpr (BATCH) return __ldg(reinterpret_cast<const float4 *>(q));
+        else return *reinterpret_cast<const float4 *>(q);
+    };
 
     const int P = a.P;
     const float invP = 1.0f / (float)P;
@@ -185,15 +213,42 @@ ipm_kernel(const IpmArgs a)
 
     // pixel work list: 0..N-1, or the first list_len entries of list
     const unsigned long long n_work = a.list ? *a.list_len : (unsigned long long)a.N;
+    // "no more work": a.N, or -1 in a batch
+    auto has = [&](long long p) -> bool { return BATCH ? p >= 0 : p < a.N; };
     auto fetch = [&]() -> long long {
-        unsigned long long v = 0;
-        long long p = a.N;                      // a.N marks "no more work"
-        if (t == 0) {
-            v = atomicAdd(a.counter, 1ULL);
-            if (v < n_work) p = a.list ? a.list[v] : (long long)v;
+        if constexpr (BATCH) {
+            // one counter over all cubes; the cube of a work index by
+            // binary search over their first indices
+            long long p = -1;
+            int c = 0;
+            if (t == 0) {
+                const unsigned long long v = atomicAdd(a.counter, 1ULL);
+                if (v < a.total) {
+                    int lo = 0, hi = a.n_cubes - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((unsigned long long)a.cubes[mid].start <= v) lo = mid; else hi = mid - 1;
+                    }
+                    c = lo;
+                    p = (long long)v - a.cubes[lo].start;
+                }
+            }
+            p = __shfl_sync(gmask, p, 0, G);
+            c = __shfl_sync(gmask, c, 0, G);
+            cb = a.cubes + c;
+            gG = cb->Ghi;
+            return p;
+        } else {
+            unsigned long long v = 0;
+            long long p = a.N;                      // a.N marks "no more work"
+            if (t == 0) {
+                v = atomicAdd(a.counter, 1ULL);
+                if (v < n_work) p = a.list ? a.list[v] : (long long)v;
+            }
+            return __shfl_sync(gmask, p, 0, G);
         }
-        return __shfl_sync(gmask, p, 0, G);
     };
+    auto chi = [&]() -> const float * { if constexpr (BATCH) return cb->c_hi; else return a.c_hi; };
 
     // load c~ and either the start point (phase A) or the saved state (B)
     auto load_pixel = [&](long long p) {
@@ -207,7 +262,8 @@ ipm_kernel(const IpmArgs a)
             float gmin = 3.4e38f, g0[NS];
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                g0[s] = valid[s] ? sGrs[s * G + t] - __ldg(a.c_hi + base + s * G + t) : 0.f;
+                const float gr = BATCH ? __ldg(cb->grs + s * G + t) : sGrs[s * G + t];
+                g0[s] = valid[s] ? gr - __ldg(chi() + base + s * G + t) : 0.f;
                 if (valid[s]) gmin = fminf(gmin, g0[s]);
             }
             for (int off = 1; off < G; off <<= 1)
@@ -232,7 +288,7 @@ ipm_kernel(const IpmArgs a)
     };
 
     long long pix = fetch();
-    bool alive = pix < a.N;
+    bool alive = has(pix);
     if (alive) load_pixel(pix);
     else {
 #pragma unroll
@@ -251,15 +307,19 @@ ipm_kernel(const IpmArgs a)
         for (int s = 0; s < NS; ++s) xbuf[s * G + t] = x[s];
         __syncwarp();
         if (!ACC) {
-            float acc[NS];
+            // c~ loads issued first: their latency overlaps the dot products
+            float acc[NS], cc[NS];
 #pragma unroll
-            for (int s = 0; s < NS; ++s) acc[s] = 0.f;
+            for (int s = 0; s < NS; ++s) {
+                acc[s] = 0.f;
+                cc[s] = valid[s] ? __ldg(chi() + cbase + s * G + t) : 0.f;
+            }
 #pragma unroll 1
             for (int j4 = 0; j4 < PP / 4; ++j4) {
                 const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    const float4 g = *reinterpret_cast<const float4 *>(sGhi + (s * G + t) * PP + 4 * j4);
+                    const float4 g = ldG4(gG + (s * G + t) * PP + 4 * j4);
                     acc[s] = fmaf(g.x, xv.x, acc[s]);
                     acc[s] = fmaf(g.y, xv.y, acc[s]);
                     acc[s] = fmaf(g.z, xv.z, acc[s]);
@@ -268,7 +328,7 @@ ipm_kernel(const IpmArgs a)
             }
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                const float gx = acc[s] - (valid[s] ? __ldg(a.c_hi + cbase + s * G + t) : 0.f);
+                const float gx = acc[s] - cc[s];
                 rd[s] = valid[s] ? (gx - lam[s]) + nu : 0.f;
             }
         } else {
@@ -334,19 +394,20 @@ ipm_kernel(const IpmArgs a)
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     const int i = s * G + t;
-                    if (valid[s]) { a.x_state[base + i] = x[s]; a.lam_state[base + i] = lam[s]; }
+                    float *xo = BATCH ? cb->x_state : a.x_state, *lo = BATCH ? cb->lam_state : a.lam_state;
+                    if (valid[s]) { xo[base + i] = x[s]; lo[base + i] = lam[s]; }
                 }
                 const bool conv = (rdmax <= a.tol_d) && (dec <= a.tol_c);
                 if (t == 0) {
-                    a.nu_state[pix] = nu;
-                    if (!ACC) a.it_state[pix] = it;
+                    (BATCH ? cb->nu_state : a.nu_state)[pix] = nu;
+                    if (!ACC) (BATCH ? cb->it_state : a.it_state)[pix] = it;
                     else {
                         a.it_state[pix] = conv ? it : -it;
                         if (!conv) atomicAdd(a.n_notconv, 1ULL);
                     }
                 }
                 pix = fetch();
-                alive = pix < a.N;
+                alive = has(pix);
                 if (alive) load_pixel(pix);
             }
             residual();
@@ -361,10 +422,10 @@ ipm_kernel(const IpmArgs a)
         for (int s = 0; s < NS; ++s) {
             const int i = s * G + t;
             const float Ds = Dof(s);
-            const float *grow = sGhi + i * PP;
+            const float *grow = gG + i * PP;
 #pragma unroll
             for (int j4 = 0; j4 < (s + 1) * G / 4; ++j4) {
-                const float4 g = *reinterpret_cast<const float4 *>(grow + 4 * j4);
+                const float4 g = ldG4(grow + 4 * j4);
                 H[s][4 * j4 + 0] = g.x; H[s][4 * j4 + 1] = g.y;
                 H[s][4 * j4 + 2] = g.z; H[s][4 * j4 + 3] = g.w;
             }

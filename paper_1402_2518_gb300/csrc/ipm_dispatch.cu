@@ -45,4 +45,16 @@ cudaError_t launch_ipm(const Bucket &b, bool accurate, const IpmArgs &a, cudaStr
 #undef LM_CASE
 }
 
+cudaError_t launch_ipm_batch(const Bucket &b, const IpmArgs &a, cudaStream_t st)
+{
+#define LM_CASE(NS, G) \
+    case NS * 100 + G: return launch_ipm_mode<NS, G, false, true>(a, st);
+    switch (b.NS * 100 + b.G) {
+        LM_CASE(2, 4) LM_CASE(2, 8) LM_CASE(4, 4) LM_CASE(8, 4) LM_CASE(4, 8) LM_CASE(9, 4)
+        LM_CASE(5, 8) LM_CASE(6, 8) LM_CASE(3, 16) LM_CASE(4, 16)
+    default: return cudaErrorInvalidValue;
+    }
+#undef LM_CASE
+}
+
 }  // namespace lm

@@ -96,6 +96,9 @@ cudaError_t launch_project(const float *cube, long long N, int L, int P,
 struct IpmArgs;
 cudaError_t launch_ipm(const Bucket &b, bool accurate, const IpmArgs &a,
                        cudaStream_t st);
+// One float32 interior-point launch over the pixels of several cubes
+// (a.cubes, a.n_cubes, a.total; a.counter zeroed), all of bucket b.
+cudaError_t launch_ipm_batch(const Bucket &b, const IpmArgs &a, cudaStream_t st);
 
 struct CrossArgs {
     long long N;

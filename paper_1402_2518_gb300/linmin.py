@@ -42,7 +42,7 @@ EXPORTED = ("linmin_default_options", "linmin_create", "linmin_unmix", "linmin_w
             "linmin_extra_spectra", "linmin_detect", "linmin_threshold_stats",
             "linmin_thresholds", "linmin_autofit", "linmin_second_pass",
             "linmin_unmix_masked", "linmin_noalloc_scratch_bytes", "linmin_fp32_peak",
-            "linmin_live_allocations")
+            "linmin_live_allocations", "linmin_unmix_batch")
 LINMIN_NOALLOC_SCRATCH_MB = 64
 LINMIN_PHASE_RING = 32
 LINMIN_PROJ_TC = 1
@@ -123,6 +123,10 @@ def load(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
     lib.linmin_unmix.restype = ctypes.c_int
     lib.linmin_unmix_cov.argtypes = [H, P, ctypes.c_longlong, P, P, P, P, P]
     lib.linmin_unmix_cov.restype = ctypes.c_int
+    PP_ = ctypes.POINTER(ctypes.c_void_p)
+    lib.linmin_unmix_batch.argtypes = [ctypes.c_int, PP_, PP_, ctypes.POINTER(ctypes.c_longlong), PP_,
+                                       PP_, PP_, PP_, PP_]
+    lib.linmin_unmix_batch.restype = ctypes.c_int
     lib.linmin_wait.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
     lib.linmin_wait.restype = ctypes.c_int
     lib.linmin_phase_times.argtypes = [H, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
@@ -258,6 +262,23 @@ def linmin_unmix(h, cube, N: int, sigma, abundances=None, uncertainties=None,
                             _ptr(iterations, "int32"))
     if check and st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
         _check(st, h)
+    return st
+
+
+def linmin_unmix_batch(handles, cubes, Ns, sigmas, abundances, uncertainties=None,
+                       residual_rms=None, iterations=None, check: bool = True) -> int:
+    """linmin_unmix of several cubes with one interior-point launch per
+    group of equal P (device tensors; lists of equal length, entries of the
+    optional lists may be None)."""
+    n = len(handles)
+    arr = lambda vals: (ctypes.c_void_p * n)(*vals)
+    opt = lambda lst, dt="float32": None if lst is None else arr([_ptr(a, dt) for a in lst])
+    st = lib().linmin_unmix_batch(n, arr(handles), arr([_ptr(c) for c in cubes]),
+                                  (ctypes.c_longlong * n)(*[int(v) for v in Ns]),
+                                  arr([_ptr(sg) for sg in sigmas]), arr([_ptr(x) for x in abundances]),
+                                  opt(uncertainties), opt(residual_rms), opt(iterations, "int32"))
+    if check and st not in (LINMIN_OK, LINMIN_ERR_NOT_CONVERGED):
+        _check(st, handles[0])
     return st
 
 
