@@ -87,6 +87,9 @@ def ipm_traffic(n_pix: int):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--workload", default="omega", choices=["omega", "crism"],
+                    help="cube of the main leg: the OMEGA-shaped one (the metric's "
+                         "workload, default) or the CRISM-shaped one")
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -699,7 +702,10 @@ def run_detection(pkg, dev, cube, x, sx, rms, it, steps: int, hbm_peak: float,
 
 
 def main():
+    global SPEC
     args = parse()
+    if args.workload == "crism":
+        SPEC = synth.CRISM_307K
     ws, rank, local = dist_env()
     cube = synth.make_cube(SPEC, n_pix=args.pixels or None)
     if args.impl == "reference":
@@ -778,7 +784,7 @@ def main():
     peak_ffma, peak_ffma2 = pkg.linmin_fp32_peak(stream)
     fp32_peak = max(peak_ffma, peak_ffma2)
     crism = None
-    if not args.no_crism and rank == 0 and not args.pixels:
+    if not args.no_crism and rank == 0 and not args.pixels and args.workload == "omega":
         crism = run_crism(pkg, dev, max(3, args.steps // 4), fp32_peak)
     full_cov = None
     if not args.no_cov and rank == 0:
@@ -832,13 +838,16 @@ def main():
                   "bf16": "f32 (bf16 tensor-core projection, double-float crossover)"}[args.precision],
         "data": "synthetic",
         "config": {"workload": SPEC.name, "pixels": N, "L": L, "P": P,
-                   "library": "32 minerals + 4 level/slope spectra",
-                   "l2": "inputs larger than L2 (cube 193 MB), no flush",
+                   "library": (f"{SPEC.n_minerals} minerals"
+                               + (f" ({SPEC.n_near_dup} near-duplicates)" if SPEC.n_near_dup else "")
+                               + f" + {SPEC.n_extras} level/slope spectra"),
+                   "l2": (f"inputs larger than L2 (cube {N * L * 4 / 1e6:.0f} MB), no flush"
+                          if N * L * 4 > 129e6 else "cube smaller than L2 (a reduced run)"),
                    "parallelism": f"replicas x{ws}"},
         "roofline": {"kernel": "ipm (interior-point launches: all pixels + retry list)",
                      "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": ipm_traffic(N),
+                     "traffic": ipm_traffic(N) if args.workload == "omega" else None,
                      "traffic_note": "DRAM bytes of the main IPM launch (ncu on 65,536 "
                                      "pixels, scaled by pixel count)",
                      "peak_note": (f"measured by linmin_fp32_peak in this run: FFMA "

@@ -128,14 +128,14 @@ struct IpmCfg {
     // registers of H per lane (rows of (s+1)*G floats)
     static constexpr int H_REGS = NS * (NS + 1) / 2 * G;
     // Warps per block and the resident blocks per SM the register budget is
-    // sized for.  Four-lane groups run the block-panel factorisation, whose
-    // unrolled loop body is large: eight warps per block iterate in
-    // lockstep, so the two warps of each scheduler fetch the same
-    // instructions (one 8-warp block per SM above 100 registers of H, else 2).
-    // Wider groups keep 4-warp blocks (2 per SM above 100 registers of H,
-    // else 3).
-    static constexpr int WARPS = (G == 4) ? 8 : 4;
-    static constexpr int MIN_BLOCKS = (G == 4) ? (H_REGS > 100 ? 1 : 2) : (H_REGS > 100 ? 2 : 3);
+    // sized for.  Four- and eight-lane groups run the block-panel
+    // factorisation, whose unrolled loop body is large: eight warps per block
+    // iterate in lockstep, so the two warps of each scheduler fetch the same
+    // instructions (four lanes: one 8-warp block per SM above 100 registers
+    // of H, else 2; eight lanes: one).  Sixteen-lane groups keep 4-warp
+    // blocks (2 per SM above 100 registers of H, else 3).
+    static constexpr int WARPS = (G <= 8) ? 8 : 4;
+    static constexpr int MIN_BLOCKS = (G == 4) ? (H_REGS > 100 ? 1 : 2) : (G == 8 ? 1 : (H_REGS > 100 ? 2 : 3));
     static constexpr int THREADS = WARPS * 32;
     // column k of L is stored for rows alignrow(k) .. PP-1 (16-byte aligned)
     static constexpr __host__ __device__ int alignrow(int k) { return ((k + 1) / 4) * 4; }
@@ -446,6 +446,33 @@ ipm_kernel(const IpmArgs a)
 #pragma unroll
         for (int s = 0; s < NS; ++s) { B1[s] = valid[s] ? 1.f : 0.f; B2[s] = -rd[s] - lam[s]; }
         const float *lb = colbuf + t;      // L[s*G + t][k] = lb[C::coloff(k) + s*G]
+        auto inverse_blocks = [&]() {
+            // ---- inverses M_b of the G x G diagonal blocks of L, written over the
+            // blocks' strictly lower entries in the column buffer (the
+            // factorisation is done with them); diag(M_b) = 1/L_kk stays in dinv
+            // with the row's owner.  Lane t forms column t of M_b by forward
+            // substitution; the block's entries are read by the whole group
+            // (broadcast) before any lane writes.
+    #pragma unroll
+            for (int b = 0; b < NS; ++b) {
+                float dq[G], m[G];
+    #pragma unroll
+                for (int q = 0; q < G; ++q) dq[q] = __shfl_sync(FULL, dinv[b], q, G);
+    #pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    float acc = 0.f;
+    #pragma unroll
+                    for (int r = 0; r < q; ++r) acc = fmaf(colbuf[C::coloff(b * G + r) + b * G + q], m[r], acc);
+                    m[q] = (q == t) ? dinv[b] : ((q > t) ? -dq[q] * acc : 0.f);
+                }
+                __syncwarp();
+                float *ct = colbuf + C::coloff(b * G + t) + b * G;
+    #pragma unroll
+                for (int q = 1; q < G; ++q)
+                    if (q > t) ct[q] = m[q];
+            }
+            __syncwarp();
+        };
         if constexpr (G == 4) {
             // Blocks of G = 4 columns (slot b).  (A) the group's four rows of
             // the diagonal block and their right-hand sides are exchanged
@@ -561,6 +588,117 @@ ipm_kernel(const IpmArgs a)
                 }
             });
             __syncwarp();
+        } else if constexpr (G == 8) {
+            // Blocks of four columns inside slots of eight rows (two blocks
+            // per slot): the same steps as for four-lane groups.  The rows of
+            // block c are lanes t0..t0+3 (t0 = 4 (c % 2)) of slot c / 2; the
+            // panel also takes the other half of that slot when c is even.
+            // The strictly lower entries of L_bb go to the column slots; the
+            // inverses of the 8 x 8 diagonal blocks are formed afterwards.
+            constexpr int NB = PP / 4;
+            float A[4][4], rb1[4], rb2[4];
+            auto exchange = [&](auto ccc) {
+                constexpr int cc = decltype(ccc)::value, sc = cc / 2, t0 = (cc % 2) * 4;
+                if (t >= t0 && t < t0 + 4) {
+                    float *xr = xbuf + 8 * (t - t0);
+                    *reinterpret_cast<float4 *>(xr) = make_float4(H[sc][4 * cc], H[sc][4 * cc + 1], H[sc][4 * cc + 2], H[sc][4 * cc + 3]);
+                    *reinterpret_cast<float2 *>(xr + 4) = make_float2(B1[sc], B2[sc]);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float4 rv = *reinterpret_cast<const float4 *>(xbuf + 8 * p);
+                    const float2 bv = *reinterpret_cast<const float2 *>(xbuf + 8 * p + 4);
+                    A[p][0] = rv.x; A[p][1] = rv.y; A[p][2] = rv.z; A[p][3] = rv.w;
+                    rb1[p] = bv.x; rb2[p] = bv.y;
+                }
+            };
+            exchange(std::integral_constant<int, 0>{});
+            lm_static_for<NB>([&](auto ccc) {
+                constexpr int c = decltype(ccc)::value, sc = c / 2, t0 = (c % 2) * 4;
+                float dq[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float dd = A[q][q];
+#pragma unroll
+                    for (int r = 0; r < q; ++r) dd = fmaf(-A[q][r], A[q][r], dd);
+                    dd = (dd > TINY) ? dd : BIGPIV;
+                    const float rq = rsqrtf(dd);
+                    dq[q] = rq;
+#pragma unroll
+                    for (int p = q + 1; p < 4; ++p) {
+                        float v = A[p][q];
+#pragma unroll
+                        for (int r = 0; r < q; ++r) v = fmaf(-A[p][r], A[q][r], v);
+                        A[p][q] = v * rq;
+                    }
+                }
+                float z1[4], z2[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float u1 = rb1[q], u2 = rb2[q];
+#pragma unroll
+                    for (int r = 0; r < q; ++r) { u1 = fmaf(-A[q][r], z1[r], u1); u2 = fmaf(-A[q][r], z2[r], u2); }
+                    z1[q] = u1 * dq[q]; z2[q] = u2 * dq[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+#pragma unroll
+                    for (int p = q + 1; p < 4; ++p) colbuf[C::coloff(4 * c + q) + 4 * c + p] = A[p][q];
+                const int tr = t - t0;          // the lane's row in the block, if 0..3
+                if (tr >= 0 && tr < 4) {
+                    dinv[sc] = tr == 0 ? dq[0] : tr == 1 ? dq[1] : tr == 2 ? dq[2] : dq[3];
+                    B1[sc] = tr == 0 ? z1[0] : tr == 1 ? z1[1] : tr == 2 ? z1[2] : z1[3];
+                    B2[sc] = tr == 0 ? z2[0] : tr == 1 ? z2[1] : tr == 2 ? z2[2] : z2[3];
+                }
+#pragma unroll
+                for (int s = sc; s < NS; ++s) {
+                    // rows below the block: the later slots, and in slot sc
+                    // (c even) the lanes of its second half
+                    const bool row = s > sc || (t0 == 0 && t >= 4);
+                    float xq[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float v = H[s][4 * c + q];
+#pragma unroll
+                        for (int r = 0; r < q; ++r) v = fmaf(-xq[r], A[q][r], v);
+                        xq[q] = v * dq[q];
+                    }
+                    if (row) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            H[s][4 * c + q] = xq[q];
+                            colbuf[t + C::coloff(4 * c + q) + 8 * s] = xq[q];
+                            ffma2s(B1[s], B2[s], -xq[q], -xq[q], z1[q], z2[q], B1[s], B2[s]);
+                        }
+                    }
+                }
+                __syncwarp();
+                // rank-4 update of the later column blocks (in slot sc, the
+                // lanes above the panel update entries above the diagonal:
+                // never read)
+                auto update_cols = [&](int c2) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(colbuf + C::coloff(4 * c + q) + 4 * c2);
+#pragma unroll
+                        for (int s = 0; s < NS; ++s) {
+                            if (s < c2 / 2) continue;
+                            const float nl = -H[s][4 * c + q];
+                            ffma2s(H[s][4 * c2], H[s][4 * c2 + 1], nl, nl, lv.x, lv.y, H[s][4 * c2], H[s][4 * c2 + 1]);
+                            ffma2s(H[s][4 * c2 + 2], H[s][4 * c2 + 3], nl, nl, lv.z, lv.w, H[s][4 * c2 + 2], H[s][4 * c2 + 3]);
+                        }
+                    }
+                };
+                if constexpr (c + 1 < NB) {
+                    update_cols(c + 1);
+                    exchange(std::integral_constant<int, c + 1>{});
+#pragma unroll
+                    for (int c2 = c + 2; c2 < NB; ++c2) update_cols(c2);
+                }
+            });
+            __syncwarp();
+            inverse_blocks();
         } else {
             // Column k = sk*G + tk: the slot block sk is unrolled (register
             // indices of H stay compile-time), the G columns of a block share one
@@ -633,31 +771,7 @@ ipm_kernel(const IpmArgs a)
             __syncwarp();
 
 
-            // ---- inverses M_b of the G x G diagonal blocks of L, written over the
-            // blocks' strictly lower entries in the column buffer (the
-            // factorisation is done with them); diag(M_b) = 1/L_kk stays in dinv
-            // with the row's owner.  Lane t forms column t of M_b by forward
-            // substitution; the block's entries are read by the whole group
-            // (broadcast) before any lane writes.
-#pragma unroll
-            for (int b = 0; b < NS; ++b) {
-                float dq[G], m[G];
-#pragma unroll
-                for (int q = 0; q < G; ++q) dq[q] = __shfl_sync(FULL, dinv[b], q, G);
-#pragma unroll
-                for (int q = 0; q < G; ++q) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int r = 0; r < q; ++r) acc = fmaf(colbuf[C::coloff(b * G + r) + b * G + q], m[r], acc);
-                    m[q] = (q == t) ? dinv[b] : ((q > t) ? -dq[q] * acc : 0.f);
-                }
-                __syncwarp();
-                float *ct = colbuf + C::coloff(b * G + t) + b * G;
-#pragma unroll
-                for (int q = 1; q < G; ++q)
-                    if (q > t) ct[q] = m[q];
-            }
-            __syncwarp();
+            inverse_blocks();
         }
 
         // forward solve L z = v in place, by blocks of G rows: the block's G
