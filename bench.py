@@ -41,8 +41,8 @@ FP32_LANES_PER_SM = 128
 # (dram__bytes_read.sum + dram__bytes_write.sum on 65,536 pixels; traffic
 # grows with the pixel count).  Valid only for the kernel source it was
 # measured on (hash of csrc/ipm.cuh).
-IPM_TRAFFIC = {"ipm_sha256_12": "674da1bbcd7e",
-               "bytes_per_pixel": (9.579776e6 + 0.0064e6) / 65536}
+IPM_TRAFFIC = {"ipm_sha256_12": "2423e78fbf10",
+               "bytes_per_pixel": (9.549568e6 + 0.00128e6) / 65536}
 
 
 # DRAM bytes of detect_kernel (ncu, 65,536 pixels: 19,948,544 read, 0

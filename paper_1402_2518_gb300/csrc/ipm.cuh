@@ -151,12 +151,17 @@ struct IpmCfg {
     static constexpr int LBUF = colstart(PP);
     // per-group floats: L columns + a broadcast area (x in the residual, the
     // diagonal block rows in the factorisation: at least 32 floats); stride
-    // = 4 (mod 32) words so that the GPW groups of a warp hit distinct banks
-    // with LDS.128
+    // = G (mod 32) words, so that the G consecutive words the lanes of each
+    // group read or write at one offset (solves, panel stores) fall in
+    // distinct banks for the GPW groups of a warp
     static constexpr int GROUP_RAW = LBUF + (PP > 32 ? PP : 32);
-    static constexpr int GROUP_FLOATS = ((GROUP_RAW + 31) / 32) * 32 + 4;
+    static constexpr int GROUP_FLOATS = ((GROUP_RAW + 31) / 32) * 32 + G;
+    // row stride of G~ in shared memory: 4 (mod 8) words, so that the rows
+    // of consecutive lanes (read at the same column with LDS.128) start 4,
+    // 12, 20 or 28 banks apart and up to eight of them share no bank
+    static constexpr int GS = (PP % 8 == 4) ? PP : PP + 4;
     static constexpr size_t smem_bytes(bool acc) {
-        return sizeof(float) * ((acc ? 2 : 1) * PP * PP + PP +
+        return sizeof(float) * ((acc ? 2 : 1) * PP * GS + PP +
                                 (size_t)WARPS * GPW * GROUP_FLOATS);
     }
 };
@@ -172,9 +177,9 @@ ipm_kernel(const IpmArgs a)
     constexpr float TINY = 1e-30f, BIGPIV = 1e30f, DMAX = 1e30f;
 
     extern __shared__ __align__(16) float sm[];
-    float *sGhi = sm;
-    float *sGlo = sm + PP * PP;                      // only with ACC
-    float *sGrs = sm + (ACC ? 2 : 1) * PP * PP;
+    float *sGhi = sm;                                // PP rows of C::GS words
+    float *sGlo = sm + PP * C::GS;                   // only with ACC
+    float *sGrs = sm + (ACC ? 2 : 1) * PP * C::GS;
     float *grp0 = sGrs + PP;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -185,8 +190,9 @@ ipm_kernel(const IpmArgs a)
 
     if constexpr (!BATCH) {
         for (int e = threadIdx.x; e < PP * PP; e += blockDim.x) {
-            sGhi[e] = a.Ghi[e];
-            if (ACC) sGlo[e] = a.Glo[e];
+            const int r = e / PP, q = e - r * PP;
+            sGhi[r * C::GS + q] = a.Ghi[e];
+            if (ACC) sGlo[r * C::GS + q] = a.Glo[e];
         }
         for (int e = threadIdx.x; e < PP; e += blockDim.x) sGrs[e] = a.grs[e];
     }
@@ -194,6 +200,7 @@ ipm_kernel(const IpmArgs a)
     // G~ rows: shared memory, or (batch) the group's current cube in global
     // memory (read through L1)
     const float *gG = sGhi;
+    constexpr int GST = BATCH ? PP : C::GS;          // row stride of gG's rows
     const IpmCube *cb = nullptr;
     auto ldG4 = [&](const float *q) -> float4 {
         if constexpr (BATCH) return __ldg(reinterpret_cast<const float4 *>(q));
@@ -319,7 +326,7 @@ ipm_kernel(const IpmArgs a)
                 const float4 xv = *reinterpret_cast<const float4 *>(xbuf + 4 * j4);
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
-                    const float4 g = ldG4(gG + (s * G + t) * PP + 4 * j4);
+                    const float4 g = ldG4(gG + (s * G + t) * GST + 4 * j4);
                     acc[s] = fmaf(g.x, xv.x, acc[s]);
                     acc[s] = fmaf(g.y, xv.y, acc[s]);
                     acc[s] = fmaf(g.z, xv.z, acc[s]);
@@ -335,8 +342,8 @@ ipm_kernel(const IpmArgs a)
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 const int i = s * G + t;
-                const float *grow = sGhi + i * PP;
-                const float *glow = sGlo + i * PP;
+                const float *grow = sGhi + i * C::GS;
+                const float *glow = sGlo + i * C::GS;
                 dot2 d;
 #pragma unroll
                 for (int j4 = 0; j4 < PP / 4; ++j4) {
@@ -422,7 +429,7 @@ ipm_kernel(const IpmArgs a)
         for (int s = 0; s < NS; ++s) {
             const int i = s * G + t;
             const float Ds = Dof(s);
-            const float *grow = gG + i * PP;
+            const float *grow = gG + i * GST;
 #pragma unroll
             for (int j4 = 0; j4 < (s + 1) * G / 4; ++j4) {
                 const float4 g = ldG4(grow + 4 * j4);
