@@ -384,6 +384,26 @@ cudaError_t launch_project(const float *cube, long long N, int L, int P, const f
     }
 }
 
+// Warp-aggregated counting: the active lanes of a warp with the same key
+// add their count with one atomic (the leader's), every lane gets its own
+// slot: base of the leader's atomic + its rank among those lanes.
+__device__ __forceinline__ unsigned long long bucket_slot(unsigned long long *cursor, int key)
+{
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(cursor + key, (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
+}
+__device__ __forceinline__ void bucket_count(unsigned int *hist, int key)
+{
+    const unsigned act = __activemask();
+    const unsigned peers = __match_any_sync(act, key);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + key, (unsigned)__popc(peers));
+}
+
 // ------------------------------------------------ fp64 crossover/refinement
 constexpr int REF_THREADS = 128;
 
@@ -413,7 +433,7 @@ __global__ void support_kernel(long long N, int P, const float *__restrict__ x,
     mask[n] = m;
     const int kk = __popcll(m);
     ksize[n] = kk;
-    if (hist) atomicAdd(hist + kk, 1u);
+    if (hist) bucket_count(hist, kk);
 }
 
 // Bucket starts of the support sizes in decreasing order (one block): the
@@ -439,8 +459,7 @@ __global__ void bucket_scatter_kernel(long long N, const int *__restrict__ ksize
 {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const unsigned long long pos = atomicAdd(cursor + ksize[n], 1ULL);
-    list[pos] = n;
+    list[bucket_slot(cursor, ksize[n])] = n;
 }
 
 // The same counting sort for a list of pixels (the supports they have now):
@@ -454,7 +473,7 @@ __global__ void list_hist_kernel(const long long *__restrict__ list,
     if (i >= (long long)*len) return;
     const int k = __popcll(mask[list[i]]);
     ksize[i] = k;
-    atomicAdd(hist + k, 1u);
+    bucket_count(hist, k);
 }
 __global__ void list_scatter_kernel(const long long *__restrict__ list,
                                     const unsigned long long *__restrict__ len,
@@ -464,7 +483,7 @@ __global__ void list_scatter_kernel(const long long *__restrict__ list,
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (long long)*len) return;
-    out[atomicAdd(cursor + ksize[i], 1ULL)] = list[i];
+    out[bucket_slot(cursor, ksize[i])] = list[i];
 }
 
 // One pass of the active-set crossover.  For each listed pixel, solve the
