@@ -709,8 +709,8 @@ static linmin_status unmix_impl(linmin_handle h, const float *cube, long long N,
     mark(h, 6);
     if (h->opt.profile) ++h->calls;
     h->launches = (cov_inv ? PREP_COV_LAUNCHES : PREP_LAUNCHES) + proj_launches + 1 +
-                  crossover_launches(true) +
-                  2 + crossover_launches(false) + (d_rms ? 1 : 0);
+                  crossover_launches(true, P) +
+                  2 + crossover_launches(false, P) + (d_rms ? 1 : 0);
     if (d_it) LM_CUDA(h, cudaMemcpyAsync(d_it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),
                       "copy iterations");
     if (h->slack) {
@@ -825,7 +825,8 @@ static linmin_status unmix_back(linmin_ctx *h)
     mark(h, 6);
     if (h->opt.profile) ++h->calls;
     // the batch's interior-point launch is counted with the batch, not here
-    h->launches = h->pend.launches + crossover_launches(true) + 2 + crossover_launches(false) +
+    h->launches = h->pend.launches + crossover_launches(true, h->P) + 2 +
+                  crossover_launches(false, h->P) +
                   (h->pend.rms ? 1 : 0);
     if (h->pend.it)
         LM_CUDA(h, cudaMemcpyAsync(h->pend.it, h->it, (size_t)N * 4, cudaMemcpyDeviceToDevice, st),

@@ -739,12 +739,14 @@ constexpr int XG = 8;
 template <int KMAX>
 struct XGCfg {
     static constexpr int KS = (KMAX + XG - 1) / XG;        // row slots per lane
-    static constexpr int THREADS = KMAX > 48 ? 32 : 64;    // 4 or 8 groups per block
+    // 16, 8 or 4 groups per block
+    static constexpr int THREADS = KMAX <= XCAP ? 128 : (KMAX > 48 ? 32 : 64);
+    static constexpr int MIN_BLOCKS = KMAX <= XCAP ? 4 : 1;
     static constexpr int GROUPS = THREADS / XG;
-    // per group, sized by P (supports have at most P coordinates, so the
-    // occupancy follows the library rather than the bucket): L hi/lo as
-    // packed lower triangles, x hi/lo, the support list
-    static int group_words(int P) { return P * (P + 1) + 3 * P; }
+    // per group, sized by the largest support K = min(P, KMAX) this launch
+    // solves: L hi/lo as packed lower triangles, x hi/lo, the support list
+    __host__ __device__ static int kdim(int P) { return P < KMAX ? P : KMAX; }
+    static int group_words(int P) { return kdim(P) * (kdim(P) + 1) + 3 * kdim(P); }
     static size_t smem(int P) { return sizeof(float) * (2 * (size_t)P * P + (size_t)GROUPS * group_words(P)); }
 };
 
@@ -773,7 +775,7 @@ __device__ __forceinline__ void group_argmin(unsigned mask, float &v, int &i)
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(XGCfg<KMAX>::THREADS)
+__global__ void __launch_bounds__(XGCfg<KMAX>::THREADS, XGCfg<KMAX>::MIN_BLOCKS)
 crossover_group_kernel(const CrossArgs a)
 {
     using C = XGCfg<KMAX>;
@@ -790,23 +792,35 @@ crossover_group_kernel(const CrossArgs a)
     }
     const int lane = threadIdx.x & 31, t = lane % XG, grp = threadIdx.x / XG;
     const unsigned gmask = ((1u << XG) - 1u) << ((lane / XG) * XG);
-    const int lsz = P * (P + 1) / 2;
-    float *Lh = sgm + 2 * P * P + (size_t)grp * (2 * lsz + 3 * P);
-    float *Ll = Lh + lsz, *xh = Ll + lsz, *xl = xh + P;
-    int *sidx = reinterpret_cast<int *>(xl + P);
+    const int K = C::kdim(P), lsz = K * (K + 1) / 2;
+    float *Lh = sgm + 2 * P * P + (size_t)grp * (2 * lsz + 3 * K);
+    float *Ll = Lh + lsz, *xh = Ll + lsz, *xl = xh + K;
+    int *sidx = reinterpret_cast<int *>(xl + K);
     __syncthreads();
     const df zero = df_make(0.f);
     const long long stride = (long long)gridDim.x * C::GROUPS;
     for (long long slot = (long long)blockIdx.x * C::GROUPS + grp; slot < (long long)n_work;
          slot += stride) {
-        const long long n = a.list_in[slot];
+        // a list entry: the pixel, and above XG_SOLVE_SHIFT the solves it
+        // already had (entries handed over from a launch with a smaller K)
+        const long long entry = a.list_in[slot];
+        const long long n = entry & ((1LL << XG_SOLVE_SHIFT) - 1);
         const size_t base = (size_t)n * P;
         unsigned long long m = a.mask[n];
         // up to max_solves support solves for this pixel: each failed KKT
         // check flips one coordinate and solves again on the new support
-        for (int solve = 0;; ++solve) {
+        for (int solve = (int)(entry >> XG_SOLVE_SHIFT);; ++solve) {
             const bool can_flip = solve + 1 < a.max_solves;
             const int k = __popcll(m);
+            if (k > KMAX) {
+                // more coordinates than this launch's factor holds: the pixel,
+                // its support already in mask[n], goes to the launch sized by P
+                if (t == 0) {
+                    const unsigned long long pos = atomicAdd(a.over_len, 1ULL);
+                    a.over_list[pos] = n | ((long long)solve << XG_SOLVE_SHIFT);
+                }
+                break;
+            }
             // row slots in use: the slot loops (unrolled to KS) stop there
             const int ks = (k + XG - 1) / XG;
             for (int i = t; i < P; i += XG)
@@ -1088,12 +1102,31 @@ static cudaError_t launch_group_t(const CrossArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-static cudaError_t launch_pass_group(const CrossArgs &a, cudaStream_t st)
+static cudaError_t launch_group_full(const CrossArgs &a, cudaStream_t st)
 {
     if (a.P <= 16) return launch_group_t<16>(a, st);
     if (a.P <= 32) return launch_group_t<32>(a, st);
     if (a.P <= 48) return launch_group_t<48>(a, st);
     return launch_group_t<64>(a, st);
+}
+
+// Lane groups over a.list_in.  For P > XCAP a first launch factors supports
+// of up to XCAP coordinates (a third to a half of the shared memory per group
+// at P = 36 to 48, so more groups per SM); the rare pixel whose support
+// outgrows that is listed in w.list[1] with its solve count and finished by
+// a launch sized by P.  w.list[1] and w.len[2] are free at this point.
+static cudaError_t launch_pass_group(const CrossArgs &a, const CrossoverScratch &w, cudaStream_t st)
+{
+    if (a.P <= XCAP) return launch_group_full(a, st);
+    CrossArgs c = a;
+    c.over_list = w.list[1];
+    c.over_len = w.len + 2;
+    cudaError_t e = launch_group_t<XCAP>(c, st);
+    if (e != cudaSuccess) return e;
+    CrossArgs o = a;
+    o.list_in = w.list[1];
+    o.len_in = w.len + 2;
+    return launch_group_full(o, st);
 }
 
 cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
@@ -1154,7 +1187,7 @@ cudaError_t launch_crossover(const CrossArgs &base, const CrossoverScratch &w,
     }
     a.list_out = nullptr;
     a.len_out = nullptr;
-    return launch_pass_group(a, st);
+    return launch_pass_group(a, w, st);
 }
 
 // ------------------------------------------------------------------- rms

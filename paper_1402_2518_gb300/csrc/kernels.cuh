@@ -47,7 +47,17 @@ struct Prep {
 // them so that the launch count the C ABI reports stays exact)
 constexpr int PREP_LAUNCHES = 3;
 constexpr int PREP_COV_LAUNCHES = 4;
-constexpr int crossover_launches(bool whole_cube) { return whole_cube ? 3 + 3 + 2 : 1 + 1; }
+// The lane-group launch of the crossover factors supports of at most XCAP
+// coordinates in its shared memory when P > XCAP (more groups per SM); a
+// pixel whose support outgrows that goes on to a second launch sized by P.
+constexpr int XCAP = 24;
+// list entries of that handoff: pixel | (solves done << XG_SOLVE_SHIFT);
+// pixel indices stay below 2^40
+constexpr int XG_SOLVE_SHIFT = 56;
+constexpr int crossover_launches(bool whole_cube, int P)
+{
+    return (whole_cube ? 3 + 3 + 2 : 1 + 1) + (P > XCAP ? 1 : 0);
+}
 
 cudaError_t launch_prep(const float *S, const float *sigma, int L, int P, int PP,
                         const Prep &o, cudaStream_t st);
@@ -117,6 +127,8 @@ struct CrossArgs {
     const unsigned long long *len_in;
     long long *list_out;           // pixels handed to the next pass
     unsigned long long *len_out;
+    long long *over_list = nullptr;          // lane groups with K < P: pixels whose
+    unsigned long long *over_len = nullptr;  // support outgrew K (set by launch_crossover)
     long long *retry_list;         // pixels the crossover could not finish (or NULL)
     unsigned long long *retry_len;
     unsigned long long *n_unverified;   // counted when retry_list is NULL

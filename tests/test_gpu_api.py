@@ -36,11 +36,12 @@ def test_phase_ring_and_launch_count():
     # prep 3, projection (tensor cores: B~ exponents and slices, pixel
     # exponents, GEMM),
     # IPM, crossover (support, scan, scatter, pass 0, sort of its flips: histogram,
-    # scan, scatter; lane groups), retry
-    # (2 IPM, support, lane groups), rms
-    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 8 + 2 + 2 + 1
+    # scan, scatter; lane groups for supports of up to 24 coordinates, then
+    # for larger ones: P = 36), retry
+    # (2 IPM, support, the two lane-group launches), rms
+    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 9 + 2 + 3 + 1
     assert pkg.linmin_unmix(h, X, cube.N, sg, x) == 0          # no RMS requested
-    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 8 + 2 + 2
+    assert pkg.linmin_last_launches(h) == 3 + 4 + 1 + 9 + 2 + 3
     assert pkg.linmin_unmix(h, X, 0, sg, x) == 0
     assert pkg.linmin_last_launches(h) == 0
     st, _ = um.wait()

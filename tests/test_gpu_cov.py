@@ -60,7 +60,7 @@ def test_cov_prefix_elementwise(pkg, spec, rho):
     cube, C, Ci = synth.make_cube_cov(spec, rho, n_pix=1200)
     st, nbad, launches, got = run_cov(pkg, cube.S, Ci, cube.X)
     assert st == 0 and nbad == 0
-    assert launches == 4 + 4 + 1 + 8 + 2 + 2 + 1         # cov prep 4, tensor-core projection 4
+    assert launches == 4 + 4 + 1 + 9 + 2 + 3 + 1         # cov prep 4, tensor-core projection 4
     ref = oracle.unmix_cov(cube.S, Ci, cube.X)
     check(cube.S, Ci, cube.X, got, ref, np.arange(cube.N))
 

@@ -145,6 +145,20 @@ def test_large_libraries(pkg, P):
     check(gpu, ref, cube.S, cube.sigma, cube.X)
 
 
+@pytest.mark.parametrize("P,L,seed", [(36, 184, 1036), (48, 240, 1048)])
+def test_large_supports(pkg, P, L, seed):
+    """Every library column in play (kmax = P) and little noise: about a
+    third (P = 36) to two thirds (P = 48) of the solutions have more than 24
+    coordinates on their support, so the crossover's lane groups hand those
+    pixels from the launch that holds supports of at most 24 coordinates to
+    the one sized by P."""
+    cube = synth.random_instance(seed, 700, L, P, kmax=P, sigma_const=5e-4)
+    ref = oracle.unmix(cube.S, cube.sigma, cube.X)
+    assert np.mean(np.asarray(ref["ksup"]) > 24) > 0.25
+    gpu = run_gpu(pkg, cube.S, cube.sigma, cube.X)
+    check(gpu, ref, cube.S, cube.sigma, cube.X)
+
+
 def test_P1_and_N1(pkg):
     rng = np.random.Generator(np.random.PCG64(7))
     S = rng.uniform(0.2, 0.6, (1, 20)).astype(np.float32)

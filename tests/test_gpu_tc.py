@@ -45,7 +45,7 @@ def test_tc_prefix_elementwise(pkg, spec):
     ref = oracle.unmix(cube.S, cube.sigma, cube.X)
     gpu = run(pkg, cube.S, cube.sigma, cube.X, linmin.LINMIN_PROJ_TC)
     assert gpu["status"] == 0
-    assert gpu["launches"] == 3 + 4 + 1 + 8 + 2 + 2 + 1
+    assert gpu["launches"] == 3 + 4 + 1 + 9 + 2 + 3 + 1
     check(gpu, ref, cube.S, cube.sigma, cube.X)
 
 
