@@ -251,10 +251,11 @@ LINMIN_API const char *linmin_last_error(linmin_handle h);
 /* Number of kernel launches the last linmin_unmix on h queued (0 before the
  * first call or for N = 0; -1 for a NULL handle).  A fixed pipeline: 3
  * preparation kernels, the projection, the interior-point kernel, the
- * crossover (support, counting sort, a pass over every pixel and one
- * launch of lane groups that takes the pixels it could not finish through
- * further support changes), the retry path (two interior-point kernels,
- * support, lane groups) and the RMS. */
+ * crossover (support, counting sort, a pass over every pixel and the
+ * lane groups that take the pixels it could not finish through further
+ * support changes: one launch, or for P > 24 two, the first for supports
+ * of at most 24 coordinates), the retry path (two interior-point kernels,
+ * support, the same lane-group launches) and the RMS. */
 LINMIN_API int linmin_last_launches(linmin_handle h);
 
 /* Lanes per pixel (G) of the interior-point kernel the handle runs: a
