@@ -914,6 +914,7 @@ linmin_status linmin_unmix_batch(int n, const linmin_handle *handles, const floa
     const size_t counters = sizeof(unsigned long long) * groups.size();
     const size_t need = counters + sizeof(IpmCube) * desc.size();
     if (need > h0->bdesc_cap) {
+        h0->bdesc_cap = 0;                 // dalloc frees the old buffer first
         LM_CUDA(h0, dalloc(h0, &h0->bdesc, need), "batch descriptors");
         h0->bdesc_cap = need;
     }
