@@ -223,6 +223,37 @@ def test_against_augmented_nnls():
         np.testing.assert_allclose(r["x"][n], xn, atol=2e-6)
 
 
+@pytest.mark.parametrize("P,L,seed", [(36, 184, 1036), (48, 240, 1048)])
+def test_large_supports_certified(P, L, seed):
+    """Every library column in play (kmax = P) and little noise, the inputs
+    of the device's large-support parity case: a quarter to a half of the
+    solutions have more than 24 coordinates on their support.  Feasibility,
+    a Frank-Wolfe gap ~ 0, the KKT conditions and the augmented NNLS (which
+    shares nothing with the interior point) fix the oracle's x there."""
+    nnls = pytest.importorskip("scipy.optimize").nnls
+    cube = synth.random_instance(seed, 700, L, P, kmax=P, sigma_const=5e-4)
+    rows = np.arange(0, cube.N, 7)
+    r = oracle.unmix(cube.S, cube.sigma, cube.X[rows])
+    assert np.all(r["iters"] >= 0)
+    assert np.mean(np.asarray(r["ksup"]) > 24) > 0.2
+    G, B = _pins.whiten(cube.S, cube.sigma)
+    scale = np.max(np.diag(G))
+    w = 1.0 / cube.sigma.astype(np.float64)
+    Aw = (cube.S.astype(np.float64) * w).T
+    delta = 1e4 * np.sqrt(np.max(np.sum(Aw * Aw, axis=0)))
+    Aaug = np.vstack([Aw, delta * np.ones((1, cube.P))])
+    for k, n in enumerate(rows):
+        x = r["x"][k]
+        y = cube.X[n].astype(np.float64)
+        c = B @ y
+        assert abs(x.sum() - 1.0) <= 1e-12 and x.min() >= 0.0
+        assert _pins.fw_gap(G, c, x) <= 1e-9 * scale
+        stat, dual = _pins.kkt_violation(G, c, x, support_tol=1e-9)
+        assert stat <= 1e-6 * scale and dual <= 1e-6 * scale
+        xn, _ = nnls(Aaug, np.concatenate([y * w, [delta]]), maxiter=50 * cube.P)
+        np.testing.assert_allclose(x, xn, atol=2e-6)
+
+
 def test_non_unique_library_detected():
     """The paper's +-cos/+-sin extras (Appendix, ids 37-44) sum to zero in
     pairs; two such pairs give a null direction d of S^T with 1^T d = 0, so
