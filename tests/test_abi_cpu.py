@@ -85,6 +85,11 @@ def test_invalid_arguments_rejected_on_host():
                              ctypes.byref(h)) == linmin.LINMIN_ERR_INVALID
     assert lib.linmin_unmix(None, None, 0, None, None, None, None, None) == \
         linmin.LINMIN_ERR_INVALID
+    # the batch call: no cubes, or a NULL handle in the list
+    assert lib.linmin_unmix_batch(0, None, None, None, None, None, None, None, None) == \
+        linmin.LINMIN_ERR_INVALID
+    assert lib.linmin_unmix_batch(1, (ctypes.c_void_p * 1)(None), None, None, None, None, None,
+                                  None, None) == linmin.LINMIN_ERR_INVALID
     assert lib.linmin_destroy(None) == linmin.LINMIN_OK
 
 
